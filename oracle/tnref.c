@@ -1,0 +1,362 @@
+/*
+ * tnref -- CPU oracle for temporal out-components and network hashing.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, obviously correct
+ * reference that the GPU library is checked against.  Only the test suite, the
+ * package smoke check and the benchmark's CPU-baseline leg may load it; the
+ * product path never does.  It shares no code, header or table with the GPU
+ * library.
+ *
+ * Conventions (paper Section 2.1): an event e = (u, v, t) is an undirected
+ * interaction between nodes u, v in [0, n) at integer time t; events arrive
+ * sorted by non-decreasing t.  Two events are adjacent only when they share a
+ * node AND their times differ (dt > 0), so events with equal timestamps never
+ * chain.  A "component matrix" has n rows of `width` uint64 words (row stride =
+ * width, no padding); bit c of row i is (S[i*width + c/64] >> (c%64)) & 1 and
+ * means "node i has been reached from source column c" (Section 3.1: row i is
+ * the in-component of i, column j the out-component of j).
+ *
+ * Readings of the paper that this file fixes (the paper is silent or garbled):
+ *  - equal timestamps: a group G of events with the same t is applied as one
+ *    snapshot, S_new[x] = S_old[x] OR (OR over e in G touching x of
+ *    S_old[other end of e]).  With distinct timestamps this is exactly
+ *    Algorithm 1 (one event at a time: r = S[u] | S[v]; S[u] = S[v] = r).
+ *  - self-loops and duplicate events are harmless no-ops of the same rule.
+ *  - the hash is Thorup-Zhang 2-character tabulation with derived character
+ *    (Section 4.1), tables filled by degree-3 polynomials modulo 2^61-1 whose
+ *    coefficients come from a SplitMix64 stream reduced modulo 2^31-1.
+ *
+ * Parity status: the component matrix, its sizes, the recombination and the
+ * brute-force SI simulation are pinned by the tests (closed forms, brute force,
+ * invariants).  The hash's exact constants are a project definition: its
+ * structure and 4-wise independence are pinned, but agreement with the
+ * authors' own (unpublished) hash values is "parity unpinned".
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define TNREF_OK 0
+#define TNREF_EINVAL (-1)
+#define TNREF_ERANGE (-2)
+#define TNREF_EORDER (-3)
+#define TNREF_ENOMEM (-4)
+
+/* ---------------------------------------------------------------------------
+ * Input checks (Section 2.1: nodes are labelled [0, n), events are time
+ * ordered).
+ * ------------------------------------------------------------------------- */
+int tnref_validate(const uint32_t *u, const uint32_t *v, const int64_t *t,
+                   uint64_t m, uint32_t n)
+{
+    for (uint64_t e = 0; e < m; ++e) {
+        if (u[e] >= n || v[e] >= n)
+            return TNREF_ERANGE;
+        if (e > 0 && t[e] < t[e - 1])
+            return TNREF_EORDER;
+    }
+    return TNREF_OK;
+}
+
+/* ---------------------------------------------------------------------------
+ * Initial state (Algorithm 1, first line: S <- I_n).  Column c of the matrix
+ * is the out-component of source node src[c]; with src == NULL the sources are
+ * all n nodes in order and the result is the identity matrix.  Columns not
+ * covered by a source stay zero.
+ * ------------------------------------------------------------------------- */
+void tnref_init_sources(uint64_t *S, uint32_t n, uint64_t width,
+                        const uint32_t *src, uint64_t nsrc)
+{
+    memset(S, 0, (size_t)n * width * sizeof(uint64_t));
+    if (src == NULL) {
+        for (uint32_t i = 0; i < n; ++i)
+            S[(uint64_t)i * width + i / 64] |= 1ull << (i % 64);
+    } else {
+        for (uint64_t c = 0; c < nsrc; ++c)
+            S[(uint64_t)src[c] * width + c / 64] |= 1ull << (c % 64);
+    }
+}
+
+/* ---------------------------------------------------------------------------
+ * The matrix algorithm (Algorithm 1, Section 3.1) with equal-timestamp groups
+ * applied as snapshots (adjacency requires dt > 0, Section 2.1).
+ *
+ * For each group G of equal t, in time order:
+ *   old[x] = S[x] for every node x touched by G;
+ *   for each event (a, b) in G:  S[a] |= old[b];  S[b] |= old[a].
+ * Because S[a] already contains old[a], a singleton group gives
+ * S[a] = S[b] = old[a] | old[b], which is Algorithm 1's update.
+ * ------------------------------------------------------------------------- */
+int tnref_apply_events(const uint32_t *u, const uint32_t *v, const int64_t *t,
+                       uint64_t m, uint32_t n, uint64_t *S, uint64_t width)
+{
+    if (m == 0)
+        return TNREF_OK;
+    int rc = tnref_validate(u, v, t, m, n);
+    if (rc != TNREF_OK)
+        return rc;
+
+    int64_t *slot = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    uint32_t *touched = NULL;
+    uint64_t *old = NULL;
+    uint64_t cap = 0;
+    if (!slot)
+        return TNREF_ENOMEM;
+    for (uint32_t i = 0; i < n; ++i)
+        slot[i] = -1;
+
+    uint64_t g0 = 0;
+    while (g0 < m) {
+        uint64_t g1 = g0 + 1;
+        while (g1 < m && t[g1] == t[g0])
+            ++g1;
+        uint64_t need = 2 * (g1 - g0);
+        if (need > cap) {
+            free(touched);
+            free(old);
+            cap = need;
+            touched = (uint32_t *)malloc(cap * sizeof(uint32_t));
+            old = (uint64_t *)malloc(cap * width * sizeof(uint64_t));
+            if (!touched || !old) {
+                free(slot);
+                free(touched);
+                free(old);
+                return TNREF_ENOMEM;
+            }
+        }
+        /* snapshot the rows of the group's nodes */
+        uint64_t nt = 0;
+        for (uint64_t e = g0; e < g1; ++e) {
+            uint32_t ends[2] = {u[e], v[e]};
+            for (int q = 0; q < 2; ++q) {
+                uint32_t x = ends[q];
+                if (slot[x] < 0) {
+                    slot[x] = (int64_t)nt;
+                    touched[nt] = x;
+                    memcpy(old + nt * width, S + (uint64_t)x * width,
+                           width * sizeof(uint64_t));
+                    ++nt;
+                }
+            }
+        }
+        /* OR the partners' old rows into each endpoint */
+        for (uint64_t e = g0; e < g1; ++e) {
+            uint64_t *ra = S + (uint64_t)u[e] * width;
+            uint64_t *rb = S + (uint64_t)v[e] * width;
+            const uint64_t *oa = old + (uint64_t)slot[u[e]] * width;
+            const uint64_t *ob = old + (uint64_t)slot[v[e]] * width;
+            for (uint64_t w = 0; w < width; ++w) {
+                ra[w] |= ob[w];
+                rb[w] |= oa[w];
+            }
+        }
+        for (uint64_t k = 0; k < nt; ++k)
+            slot[touched[k]] = -1;
+        g0 = g1;
+    }
+    free(slot);
+    free(touched);
+    free(old);
+    return TNREF_OK;
+}
+
+/* ---------------------------------------------------------------------------
+ * Brute-force deterministic SI process from one source (Section 1: the
+ * simple method that simulates spreading from every node at its first
+ * appearance).  A susceptible node becomes infected when it interacts with a
+ * node that was infected before the interaction's timestamp (equal timestamps
+ * do not chain).  reached[i] = 1 iff node i is in the out-component of
+ * `source`.  O(m) per source.
+ * ------------------------------------------------------------------------- */
+int tnref_si_reach(const uint32_t *u, const uint32_t *v, const int64_t *t,
+                   uint64_t m, uint32_t n, uint32_t source, uint8_t *reached)
+{
+    if (source >= n)
+        return TNREF_EINVAL;
+    int rc = tnref_validate(u, v, t, m, n);
+    if (rc != TNREF_OK)
+        return rc;
+    memset(reached, 0, n);
+    reached[source] = 1;
+    uint8_t *fresh = (uint8_t *)calloc(n, 1);
+    if (!fresh)
+        return TNREF_ENOMEM;
+    uint64_t g0 = 0;
+    while (g0 < m) {
+        uint64_t g1 = g0 + 1;
+        while (g1 < m && t[g1] == t[g0])
+            ++g1;
+        /* infections decided on the state before this timestamp */
+        for (uint64_t e = g0; e < g1; ++e) {
+            if (reached[u[e]])
+                fresh[v[e]] = 1;
+            if (reached[v[e]])
+                fresh[u[e]] = 1;
+        }
+        for (uint64_t e = g0; e < g1; ++e) {
+            if (fresh[u[e]]) {
+                reached[u[e]] = 1;
+                fresh[u[e]] = 0;
+            }
+            if (fresh[v[e]]) {
+                reached[v[e]] = 1;
+                fresh[v[e]] = 0;
+            }
+        }
+        g0 = g1;
+    }
+    free(fresh);
+    return TNREF_OK;
+}
+
+/* ---------------------------------------------------------------------------
+ * Component sizes (Section 3, "count the number of ones in the corresponding
+ * column"; eq. for s_t: row sums and column sums have the same total).
+ * out[c] = number of rows with bit c set (out-component size of column c);
+ * in[i]  = number of bits set in row i (in-component size of node i).
+ * ------------------------------------------------------------------------- */
+void tnref_column_counts(const uint64_t *S, uint32_t n_rows, uint64_t width,
+                         uint64_t ncols, uint32_t *out)
+{
+    for (uint64_t c = 0; c < ncols; ++c) {
+        uint32_t cnt = 0;
+        for (uint32_t i = 0; i < n_rows; ++i)
+            cnt += (uint32_t)((S[(uint64_t)i * width + c / 64] >> (c % 64)) & 1u);
+        out[c] = cnt;
+    }
+}
+
+void tnref_row_counts(const uint64_t *S, uint32_t n_rows, uint64_t width,
+                      uint32_t *in)
+{
+    for (uint32_t i = 0; i < n_rows; ++i) {
+        uint32_t cnt = 0;
+        for (uint64_t c = 0; c < 64 * width; ++c)
+            cnt += (uint32_t)((S[(uint64_t)i * width + c / 64] >> (c % 64)) & 1u);
+        in[i] = cnt;
+    }
+}
+
+/* Largest out-component: the first column index holding the maximum size. */
+uint64_t tnref_argmax(const uint32_t *sizes, uint64_t count)
+{
+    uint64_t best = 0;
+    for (uint64_t c = 1; c < count; ++c)
+        if (sizes[c] > sizes[best])
+            best = c;
+    return best;
+}
+
+/* ---------------------------------------------------------------------------
+ * Network hashing (Section 4.1).
+ *
+ * Prime p = 2^61 - 1, order 4 (degree-3 polynomials: 4-universal tables).
+ * Coefficients A(i, c), i in {0,1,2}, c in [0, 4):
+ *     A(i, c) = ((r1 << 32) + r2) mod p,   r = rand(2^31 - 1).
+ * rand is read as a SplitMix64 stream reduced modulo 2^31 - 1.  Replica j's
+ * stream starts from state splitmix64(seed XOR j); draws are taken in the
+ * order i = 0..2, c = 0..3, r1 before r2.
+ * Table value T_i[x]: start from A(i, 0) and apply acc <- (x * acc + A(i, c))
+ * mod p for c = 1..3 (the MultAddMod recursion, order - 1 = 3 times).
+ * Key split for a 32-bit node id u: x0 = u & 0xFFFF, x1 = u >> 16,
+ * x2 = x0 + x1 (a 17-bit derived character, no wrap).
+ * h(u) = (T0[x0] XOR T1[x1] XOR T2[x2]) mod k.
+ * ------------------------------------------------------------------------- */
+#define TNREF_P61 ((1ull << 61) - 1)
+
+static uint64_t splitmix64_next(uint64_t *state)
+{
+    /* SplitMix64 (Steele, Lea and Flood, "Fast splittable pseudorandom
+     * number generators", OOPSLA 2014): Weyl increment then a finaliser. */
+    uint64_t z = (*state += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+void tnref_hash_coeffs(uint64_t seed, uint32_t replica, uint64_t A[12])
+{
+    uint64_t st = seed ^ (uint64_t)replica;
+    uint64_t stream = splitmix64_next(&st);
+    for (int i = 0; i < 3; ++i) {
+        for (int c = 0; c < 4; ++c) {
+            uint64_t r1 = splitmix64_next(&stream) % 2147483647ull;
+            uint64_t r2 = splitmix64_next(&stream) % 2147483647ull;
+            A[i * 4 + c] = ((r1 << 32) + r2) % TNREF_P61;
+        }
+    }
+}
+
+uint64_t tnref_table_value(const uint64_t *Ai, uint64_t x)
+{
+    unsigned __int128 acc = Ai[0];
+    for (int c = 1; c < 4; ++c)
+        acc = (acc * x + Ai[c]) % TNREF_P61;
+    return (uint64_t)acc;
+}
+
+uint64_t tnref_hash_raw(const uint64_t A[12], uint32_t u)
+{
+    uint64_t x0 = u & 0xFFFFu, x1 = u >> 16, x2 = x0 + x1;
+    return tnref_table_value(A + 0, x0) ^ tnref_table_value(A + 4, x1) ^
+           tnref_table_value(A + 8, x2);
+}
+
+/* H[j*n + x] = h_j(x) for replicas j < R and nodes x < n. */
+int tnref_hash_nodes(uint64_t seed, uint32_t R, uint32_t k, uint32_t n,
+                     uint32_t *H)
+{
+    if (k == 0)
+        return TNREF_EINVAL;
+    for (uint32_t j = 0; j < R; ++j) {
+        uint64_t A[12];
+        tnref_hash_coeffs(seed, j, A);
+        for (uint32_t x = 0; x < n; ++x)
+            H[(uint64_t)j * n + x] = (uint32_t)(tnref_hash_raw(A, x) % k);
+    }
+    return TNREF_OK;
+}
+
+/* Super-events (h(u), h(v), t) of one hashed network (Section 4.1). */
+void tnref_proxy_events(const uint32_t *u, const uint32_t *v, uint64_t m,
+                        const uint32_t *Hj, uint32_t *pu, uint32_t *pv)
+{
+    for (uint64_t e = 0; e < m; ++e) {
+        pu[e] = Hj[u[e]];
+        pv[e] = Hj[v[e]];
+    }
+}
+
+/* ---------------------------------------------------------------------------
+ * Fusion (Section 4.2, eqs. DefInvHComp and DefEstOCMerge):
+ *   est(u) = | intersection over j of h_j^{-1}( OC_j( h_j(u) ) ) |.
+ * Node w lies in h_j^{-1}(OC_j(b)) exactly when super-node h_j(w) is reached
+ * from super-node b in proxy j, i.e. bit b of row h_j(w) of P_j is set.
+ * P holds R proxy matrices, each k rows of wk = ceil(k/64) words.  Sources are
+ * src[0..nsrc) (or all n nodes when src == NULL).  O(n * nsrc * R).
+ * ------------------------------------------------------------------------- */
+int tnref_hash_estimate(const uint64_t *P, uint32_t R, uint32_t k,
+                        const uint32_t *H, uint32_t n, const uint32_t *src,
+                        uint64_t nsrc, uint32_t *est)
+{
+    uint64_t wk = (k + 63) / 64;
+    uint64_t count = src ? nsrc : n;
+    for (uint64_t s = 0; s < count; ++s) {
+        uint32_t x = src ? src[s] : (uint32_t)s;
+        if (x >= n)
+            return TNREF_ERANGE;
+        uint32_t c = 0;
+        for (uint32_t w = 0; w < n; ++w) {
+            int in_all = 1;
+            for (uint32_t j = 0; j < R && in_all; ++j) {
+                uint32_t b = H[(uint64_t)j * n + x];
+                uint32_t row = H[(uint64_t)j * n + w];
+                const uint64_t *Pj = P + (uint64_t)j * k * wk;
+                in_all = (int)((Pj[(uint64_t)row * wk + b / 64] >> (b % 64)) & 1u);
+            }
+            c += (uint32_t)in_all;
+        }
+        est[s] = c;
+    }
+    return TNREF_OK;
+}

@@ -1,0 +1,377 @@
+"""Pins for the CPU oracle (no GPU).
+
+The oracle is checked against things fixed by the paper and by mathematics,
+never against itself: hand-derived worked examples (tests/golden), brute-force
+SI simulation (Section 1), closed forms, invariants of reachability, and
+library routines for the special cases that reduce to them.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+from conftest import golden_names, load_golden
+from paper_2307_04890_gb300 import synth
+
+
+def _arrays(events):
+    ev = np.array(events, dtype=np.int64).reshape(-1, 3)
+    return ev[:, 0].astype(np.uint32), ev[:, 1].astype(np.uint32), ev[:, 2].astype(np.int64)
+
+
+def _oc_sets(S, n):
+    B = oracle.to_bool(S, n)
+    return {j: sorted(np.flatnonzero(B[:, j]).tolist()) for j in range(n)}
+
+
+# --------------------------------------------------------------------------
+# hand-derived worked examples
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("name", golden_names())
+def test_golden_examples(name):
+    n, events, oc, rows = load_golden(name)
+    u, v, t = _arrays(events)
+    S = oracle.component_matrix(u, v, t, n)
+    got = _oc_sets(S, n)
+    for j, want in oc.items():
+        assert got[j] == want, (name, j)
+        # the SI simulation from the same source agrees
+        assert sorted(np.flatnonzero(oracle.si_reach(u, v, t, n, j)).tolist()) == want
+    B = oracle.to_bool(S, n)
+    for i, want in rows.items():
+        assert sorted(np.flatnonzero(B[i]).tolist()) == want, (name, "row", i)
+
+
+# --------------------------------------------------------------------------
+# brute force: SI simulation from every source equals every column
+# --------------------------------------------------------------------------
+def _matrix_equals_si(u, v, t, n):
+    S = oracle.component_matrix(u, v, t, n)
+    B = oracle.to_bool(S, n)
+    for j in range(n):
+        si = oracle.si_reach(u, v, t, n, j)
+        if not np.array_equal(B[:, j], si):
+            return False
+    return True
+
+
+def test_exhaustive_tiny_sequences():
+    """Every event sequence of length <= 4 over the 6 links of 4 nodes, with
+    non-decreasing timestamps drawn from {0, 1, 2}."""
+    n = 4
+    links = [(a, b) for a in range(n) for b in range(a + 1, n)]
+    checked = 0
+    for length in range(1, 5):
+        for times in itertools.combinations_with_replacement(range(3), length):
+            for seq in itertools.product(links, repeat=length):
+                u = np.array([p[0] for p in seq], dtype=np.uint32)
+                v = np.array([p[1] for p in seq], dtype=np.uint32)
+                t = np.array(times, dtype=np.int64)
+                assert _matrix_equals_si(u, v, t, n), (seq, times)
+                checked += 1
+    assert checked == 21834
+
+
+@pytest.mark.parametrize("seed", range(60))
+def test_random_dense_ties_vs_si(seed):
+    rng = np.random.default_rng(1000 + seed)
+    n = int(rng.integers(2, 71))
+    m = int(rng.integers(1, 301))
+    u = rng.integers(0, n, m)
+    v = rng.integers(0, n, m)  # self-loops allowed
+    t = np.sort(rng.integers(0, int(rng.integers(1, 12)), m))
+    assert _matrix_equals_si(u.astype(np.uint32), v.astype(np.uint32), t, n)
+
+
+def test_medium_random_vs_si_sampled():
+    u, v, t = synth.uniform_events(800, 20000, t_range=5000, seed=7)
+    n = 800
+    S = oracle.component_matrix(u, v, t, n)
+    B = oracle.to_bool(S, n)
+    for j in np.random.default_rng(0).choice(n, 40, replace=False):
+        assert np.array_equal(B[:, j], oracle.si_reach(u, v, t, n, int(j)))
+
+
+# --------------------------------------------------------------------------
+# closed forms
+# --------------------------------------------------------------------------
+def test_star_distinct_times():
+    k = 50
+    u = np.zeros(k, np.uint32)
+    v = np.arange(1, k + 1, dtype=np.uint32)
+    t = np.arange(1, k + 1, dtype=np.int64)
+    sizes = oracle.column_counts(oracle.component_matrix(u, v, t, k + 1), k + 1)
+    assert sizes[0] == k + 1
+    for i in range(1, k + 1):  # leaf i meets the centre at time i, then reaches later leaves
+        assert sizes[i] == 2 + (k - i)
+
+
+def test_path_forward_and_backward():
+    k = 90
+    # forward: link (j-1, j) at time j
+    u = np.arange(0, k, dtype=np.uint32)
+    v = np.arange(1, k + 1, dtype=np.uint32)
+    t = np.arange(1, k + 1, dtype=np.int64)
+    s = oracle.column_counts(oracle.component_matrix(u, v, t, k + 1), k + 1)
+    assert s[0] == k + 1
+    assert all(s[j] == k - j + 2 for j in range(1, k + 1))
+    # backward: link (j, j+1) at time k - j, so time runs from node k down to 0
+    t2 = (k - np.arange(0, k)).astype(np.int64)
+    order = np.argsort(t2, kind="stable")
+    s2 = oracle.column_counts(oracle.component_matrix(u[order], v[order], t2[order], k + 1), k + 1)
+    assert all(s2[j] == min(j + 2, k + 1) for j in range(k + 1))
+
+
+def test_single_group_is_identity_plus_adjacency():
+    rng = np.random.default_rng(3)
+    n, m = 60, 200
+    u = rng.integers(0, n, m).astype(np.uint32)
+    v = rng.integers(0, n, m).astype(np.uint32)
+    t = np.full(m, 5, dtype=np.int64)
+    B = oracle.to_bool(oracle.component_matrix(u, v, t, n), n)
+    A = np.eye(n, dtype=bool)
+    A[u, v] = True
+    A[v, u] = True
+    assert np.array_equal(B, A)
+
+
+# --------------------------------------------------------------------------
+# invariants
+# --------------------------------------------------------------------------
+def _cfg_small(seed):
+    return synth.uniform_events(300, 6000, t_range=2000, seed=seed), 300
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_diagonal_and_row_col_sums(seed):
+    (u, v, t), n = _cfg_small(seed)
+    S = oracle.component_matrix(u, v, t, n)
+    B = oracle.to_bool(S, n)
+    assert B.diagonal().all()
+    assert oracle.column_counts(S, n).sum() == oracle.row_counts(S).sum() == B.sum()
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_concatenation_is_boolean_product(seed):
+    """Split at a boundary between timestamp groups: S_full = S_suffix (x) S_prefix."""
+    (u, v, t), n = _cfg_small(seed)
+    cut = int(np.searchsorted(t, t[len(t) // 2], side="left"))
+    Sp = oracle.to_bool(oracle.component_matrix(u[:cut], v[:cut], t[:cut], n), n).astype(np.int64)
+    Ss = oracle.to_bool(oracle.component_matrix(u[cut:], v[cut:], t[cut:], n), n).astype(np.int64)
+    Sf = oracle.to_bool(oracle.component_matrix(u, v, t, n), n)
+    assert np.array_equal((Ss @ Sp) > 0, Sf)
+
+
+def test_incremental_equals_one_shot_and_monotone():
+    (u, v, t), n = _cfg_small(5)
+    full = oracle.component_matrix(u, v, t, n)
+    S = oracle.init_sources(n)
+    prev = oracle.column_counts(S, n)
+    for a, b in synth.split_batches(t, 4):
+        oracle.apply_events(u[a:b], v[a:b], t[a:b], n, S)
+        cur = oracle.column_counts(S, n)
+        assert (cur >= prev).all()
+        prev = cur
+    assert np.array_equal(S, full)
+
+
+def test_order_inside_groups_is_irrelevant():
+    (u, v, t), n = _cfg_small(9)
+    rng = np.random.default_rng(1)
+    perm = np.lexsort((rng.random(len(t)), t))  # shuffle inside each group
+    assert np.array_equal(oracle.component_matrix(u, v, t, n),
+                          oracle.component_matrix(u[perm], v[perm], t[perm], n))
+
+
+def test_sequential_semantics_differs_on_ties():
+    """The snapshot reading matters: processing a tie group event by event
+    (plain Algorithm 1 order) would give a different matrix here."""
+    n, events, oc, _ = load_golden("star_tie.txt")
+    u, v, t = _arrays(events)
+    distinct = np.arange(len(t), dtype=np.int64)
+    B = oracle.to_bool(oracle.component_matrix(u, v, distinct, n), n)
+    assert sorted(np.flatnonzero(B[:, 2]).tolist()) != oc[2]
+
+
+def test_source_subset_equals_columns():
+    (u, v, t), n = _cfg_small(4)
+    full = oracle.to_bool(oracle.component_matrix(u, v, t, n), n)
+    src = np.random.default_rng(2).choice(n, 100, replace=False).astype(np.uint32)
+    sub = oracle.to_bool(oracle.component_matrix(u, v, t, n, src=src), len(src))
+    assert np.array_equal(sub, full[:, src])
+
+
+def test_validation_errors():
+    u = np.array([0, 1], np.uint32)
+    v = np.array([1, 5], np.uint32)
+    t = np.array([0, 1], np.int64)
+    assert oracle.validate(u, v, t, 5) == oracle.ERANGE
+    assert oracle.validate(u, v, t[::-1].copy(), 6) == oracle.EORDER
+    with pytest.raises(oracle.OracleError):
+        oracle.component_matrix(u, v, t, 5)
+
+
+def test_argmax_lowest_index():
+    assert oracle.argmax(np.array([3, 7, 7, 1], np.uint32)) == 1
+
+
+# --------------------------------------------------------------------------
+# hashing (Section 4.1)
+# --------------------------------------------------------------------------
+P61 = (1 << 61) - 1
+
+
+def test_hash_coefficients_in_field_and_distinct():
+    A0 = oracle.hash_coeffs(123, 0)
+    A1 = oracle.hash_coeffs(123, 1)
+    assert (A0 < P61).all() and (A1 < P61).all()
+    assert not np.array_equal(A0, A1)
+    assert np.array_equal(A0, oracle.hash_coeffs(123, 0))
+    assert len(set(A0.tolist())) == 12
+
+
+def test_hash_range_and_uniformity():
+    from scipy import stats
+    k, n = 64, 200_000
+    H = oracle.hash_nodes(11, 2, k, n)
+    assert H.max() < k
+    for j in range(2):
+        counts = np.bincount(H[j], minlength=k)
+        assert stats.chisquare(counts).pvalue > 1e-4
+
+
+def test_hash_pairwise_collisions():
+    k, n = 97, 4000
+    rates = []
+    for seed in range(40):
+        H = oracle.hash_nodes(seed, 1, k, n)[0]
+        rates.append((H[:-1] == H[1:]).mean())
+    assert abs(np.mean(rates) - 1 / k) < 0.25 / k
+
+
+def test_hash_tables_are_cubics_mod_p():
+    """Each table is the polynomial A0 x^3 + A1 x^2 + A2 x + A3 over GF(p)
+    (Horner recursion of MultAddMod, order 4): its constant term is A3 and its
+    third finite difference is the constant 3! * A0 (mod p)."""
+    for seed in range(5):
+        A = [int(a) for a in oracle.hash_coeffs(seed, 2)]
+        for i in range(3):
+            a0, a3 = A[4 * i], A[4 * i + 3]
+            assert oracle.table_value(oracle.hash_coeffs(seed, 2), i, 0) == a3
+            for x in (0, 1, 1000, 65530, 131068):
+                T = [oracle.table_value(oracle.hash_coeffs(seed, 2), i, x + d) for d in range(4)]
+                d3 = (T[3] - 3 * T[2] + 3 * T[1] - T[0]) % P61
+                assert d3 == (6 * a0) % P61
+
+
+def test_hash_combines_three_tables():
+    """h(u) = T0[u & 0xFFFF] ^ T1[u >> 16] ^ T2[(u & 0xFFFF) + (u >> 16)]."""
+    A = oracle.hash_coeffs(77, 0)
+    for x in (0, 1, 65535, 65536, 123456789, 2**32 - 1):
+        x0, x1 = x & 0xFFFF, x >> 16
+        want = oracle.table_value(A, 0, x0) ^ oracle.table_value(A, 1, x1) ^ oracle.table_value(A, 2, x0 + x1)
+        assert oracle.hash_raw(A, x) == want
+
+
+def test_hash_rectangle_breaks_simple_tabulation():
+    """Keys (a,c),(a,d),(b,c),(b,d) (16-bit characters) always XOR to zero under
+    simple two-table tabulation; the derived third character T2[x0+x1]
+    (Thorup-Zhang) removes that dependence, making the family 4-universal."""
+    keys = [a | (c << 16) for a in (1, 2) for c in (10, 20)]
+    zero = 0
+    patterns = np.zeros(16, dtype=np.int64)
+    seeds = 4000
+    for seed in range(seeds):
+        A = oracle.hash_coeffs(seed, 0)
+        h = [oracle.hash_raw(A, x) for x in keys]
+        zero += (h[0] ^ h[1] ^ h[2] ^ h[3]) == 0
+        bits = [x & 1 for x in h]
+        patterns[bits[0] | bits[1] << 1 | bits[2] << 2 | bits[3] << 3] += 1
+    assert zero == 0
+    from scipy import stats
+    assert stats.chisquare(patterns).pvalue > 1e-4
+
+
+# --------------------------------------------------------------------------
+# fusion (Section 4.2)
+# --------------------------------------------------------------------------
+def _hashed_case(seed, n=120, m=60, k=45, R=3):
+    """Sparse hashed networks: proxy out-components are small and the proxy
+    matrices far from symmetric, so a swapped row/column test would show."""
+    u, v, t = synth.uniform_events(n, m, t_range=300, seed=seed)
+    H = oracle.hash_nodes(seed, R, k, n)
+    P = oracle.proxy_matrices(u, v, t, H, k)
+    for j in range(R):
+        B = oracle.to_bool(P[j], k)
+        assert not np.array_equal(B, B.T) and B.mean() < 0.5
+    return u, v, t, n, k, R, H, P
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_estimate_contains_exact(seed):
+    u, v, t, n, k, R, H, P = _hashed_case(seed)
+    exact = oracle.column_counts(oracle.component_matrix(u, v, t, n), n)
+    est = oracle.hash_estimate(P, H, n)
+    assert (est >= exact).all()
+
+
+def test_estimate_matches_set_formula():
+    """|intersection_j h_j^-1(OC_j(h_j(u)))| by Python sets, with proxy
+    out-components from the SI simulation on the super-events."""
+    u, v, t, n, k, R, H, P = _hashed_case(5, n=40, m=24, k=20, R=3)
+    est = oracle.hash_estimate(P, H, n)
+    for x in range(n):
+        acc = set(range(n))
+        for j in range(R):
+            pu, pv = oracle.proxy_events(u, v, H[j])
+            oc = set(np.flatnonzero(oracle.si_reach(pu, pv, t, k, int(H[j, x]))).tolist())
+            acc &= {w for w in range(n) if int(H[j, w]) in oc}
+        assert est[x] == len(acc)
+
+
+def test_injective_hash_gives_exact():
+    u, v, t = synth.uniform_events(80, 700, t_range=200, seed=8)
+    n = 80
+    H = np.stack([np.random.default_rng(s).permutation(n) for s in range(2)]).astype(np.uint32)
+    P = oracle.proxy_matrices(u, v, t, H, n)
+    exact = oracle.column_counts(oracle.component_matrix(u, v, t, n), n)
+    assert np.array_equal(oracle.hash_estimate(P, H, n), exact)
+
+
+def test_single_replica_is_fibre_count():
+    u, v, t, n, k, R, H, P = _hashed_case(6, R=1)
+    fibre = np.bincount(H[0], minlength=k)
+    B = oracle.to_bool(P[0], k)  # B[row b, column c]: b reached from c
+    est = oracle.hash_estimate(P, H, n)
+    for x in range(n):
+        c = H[0, x]
+        assert est[x] == int((B[:, c] * fibre).sum())
+
+
+def test_more_replicas_never_increase_estimate():
+    u, v, t, n, k, R, H, P = _hashed_case(7, R=4)
+    prev = None
+    for r in range(1, R + 1):
+        est = oracle.hash_estimate(P[:r], H[:r], n)
+        if prev is not None:
+            assert (est <= prev).all()
+        prev = est
+
+
+def test_estimate_source_subset():
+    u, v, t, n, k, R, H, P = _hashed_case(2)
+    src = np.array([5, 0, 77, 119], np.uint32)
+    assert np.array_equal(oracle.hash_estimate(P, H, n, src), oracle.hash_estimate(P, H, n)[src])
+
+
+# --------------------------------------------------------------------------
+# error metric (Section 4.4)
+# --------------------------------------------------------------------------
+def test_emd_matches_scipy():
+    from scipy import stats
+    rng = np.random.default_rng(0)
+    a = rng.integers(1, 500, 1000)
+    b = rng.integers(1, 700, 1000)
+    assert oracle.emd_w1(a, b) == pytest.approx(stats.wasserstein_distance(a, b), rel=1e-12)
+    assert oracle.emd_w1(a, a) == 0.0
