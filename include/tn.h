@@ -1,0 +1,278 @@
+/*
+ * tn.h -- C ABI of the GB300 temporal out-component library (libtn).
+ *
+ * Method: "Temporal network compression via network hashing" (arXiv
+ * 2307.04890).  A temporal network is a time-ordered list of undirected events
+ * e = (u, v, t) between nodes u, v in [0, n) (Section 2.1).  Two events are
+ * adjacent when they share a node and their times differ (dt > 0); node i is
+ * reachable from node j when a time-respecting path of adjacent events leads
+ * from j to i.  The component matrix S (Section 3.1) is the n x n boolean
+ * matrix with S(i, j) = 1 iff i is reachable from j (or i == j): row i is the
+ * in-component of i, column j the out-component of j.  Algorithm 1 builds it in
+ * one pass: S <- I, then for every event r = S[u] | S[v]; S[u] = r; S[v] = r.
+ * Events sharing a timestamp are applied as one snapshot (they do not chain):
+ * S_new[x] = S_old[x] | OR over events (x, y) of the group of S_old[y].
+ *
+ * Network hashing (Section 4): R independent hash functions h_j map nodes to k
+ * super-nodes; each maps the event stream to a proxy stream (h_j(u), h_j(v), t)
+ * whose k x k component matrix P_j is computed with the same algorithm, and the
+ * out-component of u is estimated by the intersection over j of the preimages
+ * of OC_j(h_j(u)) (Section 4.2, eq. DefEstOCMerge).
+ *
+ * ---------------------------------------------------------------------------
+ * Layout of a component matrix (all entry points)
+ *   A matrix with `n_rows` rows and `ncols` source columns is stored row-major
+ *   as uint64 words.  Each row occupies tn_row_words(ncols) words (a multiple of
+ *   4 words = 32 bytes, so rows are 32-byte aligned); bit c of row i is
+ *       (S[i * tn_row_words(ncols) + c / 64] >> (c % 64)) & 1
+ *   and means "node i has been reached from source column c".  Bits at column
+ *   positions >= ncols are zero on output.  For the full matrix ncols = n and
+ *   column c is source node c.
+ *
+ * Pointers
+ *   Unless a parameter says "host", every pointer is a DEVICE pointer on the
+ *   current CUDA device, owned by the caller, and every call is enqueued on
+ *   `stream` (a cudaStream_t; NULL = the legacy default stream).  The library
+ *   keeps no reference to caller memory after a call returns, except that work
+ *   it enqueued may still be reading or writing it until the stream reaches
+ *   that point.  Scratch memory the library needs is taken from the CUDA
+ *   stream-ordered allocator on `stream` and released on the same stream.
+ *
+ * Errors
+ *   Every entry point returns a tn_status.  Host-detectable argument errors
+ *   (NULL pointers, zero sizes where not allowed, sizes beyond the limits
+ *   below) return TN_EINVAL before anything is enqueued.  Input checks that
+ *   need the data (endpoint range, time order) run on the device and are
+ *   returned synchronously by the calls documented as "validating" (they wait
+ *   for their own small validation kernel).  Errors raised later inside
+ *   asynchronous kernels (batch-order violations at apply time, bounded-wait
+ *   timeouts) are recorded in a plan status word: read them with
+ *   tn_plan_status().  No kernel of this library traps or asserts; a kernel
+ *   that hits an error condition records it and returns.
+ *
+ * Limits: n < 2^30 nodes; m < 2^30 events per call or plan; k < 2^30.
+ * Thread safety: calls on different plans and streams may run concurrently.
+ */
+#ifndef TN_H
+#define TN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t tn_status;
+
+#define TN_OK 0
+#define TN_EINVAL (-1)   /* NULL pointer, zero or out-of-limit size, bad flag */
+#define TN_ERANGE (-2)   /* an endpoint or a source id >= n */
+#define TN_EORDER (-3)   /* timestamps decrease, or a batch does not start after t_last */
+#define TN_ENOMEM (-4)   /* device scratch allocation failed */
+#define TN_ECUDA (-5)    /* a CUDA runtime call failed */
+#define TN_ETIMEOUT (-6) /* a bounded device-side wait expired */
+
+/* Flags of tn_component_matrix / tn_component_columns / tn_plan_apply. */
+#define TN_INIT_IDENTITY 1u /* initialise S first: identity, or the source columns */
+
+/* Human-readable name of a status code (static storage, never NULL). */
+const char *tn_status_string(tn_status status);
+
+/* Text of the last CUDA runtime error behind a TN_ECUDA / TN_ENOMEM returned
+ * on the calling thread (diagnostics; static storage). */
+const char *tn_last_cuda_error(void);
+
+/* Row stride, in uint64 words, of a matrix with `ncols` source columns:
+ * ceil(ncols / 256) * 4 (rows padded to 32 bytes).  tn_row_words(0) = 0. */
+uint64_t tn_row_words(uint64_t ncols);
+
+/* ---------------------------------------------------------------------------
+ * tn_component_matrix -- Algorithm 1 (Section 3.1) over one batch of events.
+ *
+ *   u, v   uint32[m] endpoints, each < n.
+ *   t      int64[m] timestamps, non-decreasing (equal values form one
+ *          snapshot group, Section 2.1: dt > 0 for adjacency).
+ *   m      number of events; m == 0 is allowed (only the init, if flagged).
+ *   n      number of nodes (rows and source columns).
+ *   S      uint64[n * tn_row_words(n)], in/out.  With TN_INIT_IDENTITY it is
+ *          first set to I_n; without it, S must hold the state reached by the
+ *          earlier batches (streaming, Section 3.5: one pass, new events
+ *          applied with the same rule).
+ *   t_last int64 scalar, in/out, may be NULL.  When given, the batch must
+ *          start strictly after *t_last (so no timestamp group is split across
+ *          batches) and *t_last is set to t[m-1] when the batch is applied.
+ *   flags  TN_INIT_IDENTITY or 0.
+ * Validating: returns TN_ERANGE / TN_EORDER synchronously (S untouched).
+ * The matrix update itself completes asynchronously on `stream`.
+ */
+tn_status tn_component_matrix(const uint32_t *u, const uint32_t *v, const int64_t *t,
+                              uint64_t m, uint32_t n, uint64_t *S, int64_t *t_last,
+                              uint32_t flags, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * tn_init_matrix -- the initial state of Algorithm 1 (S <- I_n, Section 3.1).
+ *
+ *   S      uint64[n_rows * tn_row_words(ncols)] out.
+ *   src    NULL: identity (ncols must equal n_rows); else uint32[ncols] source
+ *          ids (< n_rows): bit c of row src[c] is set, everything else cleared.
+ * Asynchronous without src; with src it is validating (an id >= n_rows
+ * returns TN_ERANGE before anything is written).  Equivalent to the TN_INIT_IDENTITY step of
+ * the calls below.
+ */
+tn_status tn_init_matrix(uint64_t *S, uint32_t n_rows, uint32_t ncols, const uint32_t *src,
+                         void *stream);
+
+/* Number of CUDA kernels this library has launched in the calling process
+ * (all threads, all devices); for accounting in benchmarks and tests. */
+uint64_t tn_kernel_launches(void);
+
+/* ---------------------------------------------------------------------------
+ * tn_component_columns -- the same algorithm restricted to the out-components
+ * of the listed sources (columns of the component matrix are independent, so
+ * any subset can be computed exactly on its own; Section 3.1).
+ *
+ *   src    uint32[nsrc] source node ids (< n, repeats allowed; an id >= n
+ *          returns TN_ERANGE); column c of S is the out-component of src[c].
+ *   S      uint64[n * tn_row_words(nsrc)], in/out; TN_INIT_IDENTITY sets bit c
+ *          of row src[c] and clears everything else.
+ * Other arguments and errors as tn_component_matrix.
+ */
+tn_status tn_component_columns(const uint32_t *u, const uint32_t *v, const int64_t *t,
+                               uint64_t m, uint32_t n, const uint32_t *src, uint32_t nsrc,
+                               uint64_t *S, int64_t *t_last, uint32_t flags, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * tn_out_sizes -- component sizes (Section 3.1: out-component size = number
+ * of ones in a column; Section 3.3, eq. for s_t: row and column sums have the
+ * same total).
+ *
+ *   S          uint64[n_rows * tn_row_words(ncols)], as produced above.
+ *   out_sizes  uint32[ncols] (required): out_sizes[c] = ones in column c.
+ *   in_sizes   uint32[n_rows] or NULL: in_sizes[i] = ones in row i.
+ *   argmax     uint32 scalar or NULL: the lowest column index holding the
+ *              largest out-component.
+ * Asynchronous; no device-side error conditions.
+ */
+tn_status tn_out_sizes(const uint64_t *S, uint32_t n_rows, uint32_t ncols,
+                       uint32_t *out_sizes, uint32_t *in_sizes, uint32_t *argmax,
+                       void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Plans: the validated, scheduled form of one event batch.  tn_plan_create
+ * checks the batch and builds its schedule once; tn_plan_apply then streams it
+ * into any matrix over the same n (identity or source columns), as often as
+ * needed, and contains no host synchronisation, so it can be captured in a
+ * CUDA graph.  The plan owns its device memory.
+ * ------------------------------------------------------------------------- */
+typedef struct tn_plan tn_plan;
+
+typedef struct tn_plan_options {
+    uint32_t window_events; /* target events per scheduling window (0 = default 2048) */
+    uint32_t slab_words;    /* 64-bit words of every row owned by one CTA when the
+                               plan is applied: 2, 4, 8 or 16 (0 = default 4) */
+    uint32_t reserved[6];   /* must be zero */
+} tn_plan_options;
+
+typedef struct tn_plan_stats {
+    uint64_t events;     /* m */
+    uint64_t windows;    /* scheduling windows */
+    uint64_t levels;     /* dependency levels (barriers per applied slab) */
+    uint64_t ops;        /* row operations after tie handling */
+    uint64_t aux;        /* source-list entries of multi-source updates */
+    uint64_t temps;      /* saved-row slots needed by tie groups (max per window) */
+    uint64_t big_windows;/* windows scheduled by the large-window path */
+    int64_t t_first, t_last;
+} tn_plan_stats;
+
+/* Validating.  u, v, t, m, n as tn_component_matrix (m >= 1).
+ * t_after: device int64 scalar or NULL; when given the batch must satisfy
+ * t[0] > *t_after (TN_EORDER otherwise).  opt may be NULL.  On success *plan
+ * receives a new plan.  The caller may free u, v, t once this call returns. */
+tn_status tn_plan_create(const uint32_t *u, const uint32_t *v, const int64_t *t,
+                         uint64_t m, uint32_t n, const int64_t *t_after,
+                         const tn_plan_options *opt, void *stream, tn_plan **plan);
+
+/* Streams the plan's events into S (layout above, ncols columns).
+ *   src    NULL for the full matrix (ncols must equal n), or uint32[ncols]
+ *          source ids for a column subset (used only with TN_INIT_IDENTITY).
+ *   t_last device int64 scalar or NULL: checked on the device
+ *          (plan t_first > *t_last, else the plan status becomes TN_EORDER and
+ *          S is left untouched) and then set to the plan's t_last.
+ * Asynchronous. */
+tn_status tn_plan_apply(const tn_plan *plan, uint64_t *S, uint32_t ncols,
+                        const uint32_t *src, int64_t *t_last, uint32_t flags,
+                        void *stream);
+
+/* One launch over several (plan, matrix) pairs (networks of different n and
+ * m, e.g. the R proxies of a hashed network): count entries of each array.
+ * Equivalent to calling tn_plan_apply on each pair; all pairs must use
+ * distinct S buffers.  Asynchronous, capturable. */
+tn_status tn_plan_apply_batch(const tn_plan *const *plans, uint64_t *const *S,
+                              const uint32_t *ncols, uint32_t count, uint32_t flags,
+                              void *stream);
+
+/* Waits for `stream`, then returns and clears the first error recorded by an
+ * asynchronous kernel that used this plan (TN_OK if none). */
+tn_status tn_plan_status(tn_plan *plan, void *stream);
+
+tn_status tn_plan_get_stats(const tn_plan *plan, tn_plan_stats *stats);
+
+/* Releases the plan; its memory is returned on `stream` after the work
+ * already enqueued there. */
+tn_status tn_plan_destroy(tn_plan *plan, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * tn_hash_proxy -- network hashing (Section 4.1).
+ *
+ * Hash family: Thorup-Zhang 2-character tabulation with a derived character.
+ * For replica j < R the coefficients A(i, c), i < 3, c < 4, are
+ * ((r1 << 32) + r2) mod (2^61 - 1) where r1, r2, ... is a SplitMix64 stream
+ * (Steele, Lea, Flood 2014) started at state splitmix64(seed XOR j) and each
+ * draw is reduced modulo 2^31 - 1; draws go in the order i, c, r1, r2.
+ * T_i[x] = A(i,0) x^3 + A(i,1) x^2 + A(i,2) x + A(i,3) mod 2^61 - 1 (Horner),
+ * and h_j(u) = (T0[u & 0xFFFF] ^ T1[u >> 16] ^ T2[(u & 0xFFFF) + (u >> 16)]) mod k.
+ *
+ *   H      uint32[R * n] out: H[j * n + x] = h_j(x).
+ *   pu, pv uint32[R * m] out, may both be NULL: the super-events of replica j
+ *          are (pu[j*m + e], pv[j*m + e], t[e]); the timestamps are unchanged.
+ *   u, v   uint32[m] endpoints (< n); may be NULL when m == 0.
+ * Asynchronous.  Endpoints >= n are not hashed: their super-events get the
+ * invalid id 0xFFFFFFFF, which a later plan over them rejects (TN_ERANGE).
+ */
+tn_status tn_hash_proxy(const uint32_t *u, const uint32_t *v, uint64_t m, uint32_t n,
+                        uint32_t k, uint32_t R, uint64_t seed, uint32_t *H,
+                        uint32_t *pu, uint32_t *pv, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * tn_hash_estimate -- fusion (Section 4.2, eqs. DefInvHComp, DefEstOCMerge):
+ *   est[s] = #{ w in [0, n) : for all j < R, bit h_j(x) of row h_j(w) of P_j }
+ * with x = src[s] (or x = s when src is NULL and nsrc == n).
+ *
+ *   P    uint64[R * k * tn_row_words(k)]: the R proxy component matrices,
+ *        each k x k in the layout above, stored one after the other.
+ *   H    uint32[R * n] as written by tn_hash_proxy.
+ *   est  uint32[nsrc] out.
+ * Asynchronous when src is NULL; validating with src (ids >= n: TN_ERANGE).
+ */
+tn_status tn_hash_estimate(const uint64_t *P, uint32_t R, uint32_t k, const uint32_t *H,
+                           uint32_t n, const uint32_t *src, uint32_t nsrc, uint32_t *est,
+                           void *stream);
+
+/* ---------------------------------------------------------------------------
+ * tn_out_component_sizes_host -- the whole exact path from HOST arrays:
+ * copies u, v, t (host, pinned or pageable) to the device, builds the
+ * component matrix from the identity, computes the out-sizes and copies them
+ * back.  out_sizes is a HOST uint32[n]; argmax a HOST uint32 or NULL.
+ * Synchronous: returns when the host outputs are written.  Device memory is
+ * taken from and returned to the stream-ordered allocator.
+ */
+tn_status tn_out_component_sizes_host(const uint32_t *u, const uint32_t *v, const int64_t *t,
+                                      uint64_t m, uint32_t n, uint32_t *out_sizes,
+                                      uint32_t *argmax, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TN_H */

@@ -1,0 +1,328 @@
+"""GB300-native temporal out-components and network hashing (arXiv 2307.04890).
+
+Thin binding over the C ABI of ``libtn.so`` (declared in ``include/tn.h``).
+Every function here only marshals arguments -- torch tensors for device
+memory, the current CUDA stream -- and calls the native entry point of the
+same name; all computation runs in the library's CUDA kernels.  Importing the
+package does not need a GPU; calling anything that launches work does, and
+raises if the native library is missing (it is never replaced by a CPU path).
+
+Matrix layout (all entry points): a component matrix with ``n_rows`` rows and
+``ncols`` source columns is an int64 tensor of shape
+``(n_rows, tn_row_words(ncols))`` holding packed bits; bit ``c`` of row ``i``
+means "node i has been reached from source column c" (Section 3.1: rows are
+in-components, columns out-components).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+__all__ = [
+    "TnError", "load_library", "tn_row_words", "tn_status_string", "tn_kernel_launches", "tn_init_matrix",
+    "tn_component_matrix", "tn_component_columns", "tn_out_sizes",
+    "tn_hash_proxy", "tn_hash_estimate", "tn_out_component_sizes_host",
+    "Plan", "tn_plan_apply_batch",
+    "TN_OK", "TN_EINVAL", "TN_ERANGE", "TN_EORDER", "TN_ENOMEM", "TN_ECUDA", "TN_ETIMEOUT",
+    "TN_INIT_IDENTITY",
+]
+
+TN_OK, TN_EINVAL, TN_ERANGE, TN_EORDER, TN_ENOMEM, TN_ECUDA, TN_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
+TN_INIT_IDENTITY = 1
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIBRARY_PATH = os.path.join(_HERE, "libtn.so")
+
+_c_u32p = ctypes.c_void_p
+_lib = None
+
+
+class TnError(RuntimeError):
+    """A libtn entry point returned a non-zero tn_status."""
+
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = _lib.tn_status_string(status).decode() if _lib else str(status)
+        if _lib and status in (TN_ECUDA, TN_ENOMEM):
+            msg += f" ({_lib.tn_last_cuda_error().decode()})"
+        super().__init__(f"{where}: {msg}")
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("window_events", ctypes.c_uint32), ("slab_words", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 6)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("events", ctypes.c_uint64), ("windows", ctypes.c_uint64), ("levels", ctypes.c_uint64),
+                ("ops", ctypes.c_uint64), ("aux", ctypes.c_uint64), ("temps", ctypes.c_uint64),
+                ("big_windows", ctypes.c_uint64), ("t_first", ctypes.c_int64), ("t_last", ctypes.c_int64)]
+
+
+def load_library(path: str | None = None):
+    """Load libtn.so (built by ``build.build_library``); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIBRARY_PATH
+    if not os.path.exists(path):
+        raise ImportError(f"libtn native library not found at {path}; build it with "
+                          "paper_2307_04890_gb300.build.build_library() (needs nvcc)")
+    lib = ctypes.CDLL(path)
+    vp, u32, u64, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32
+    sigs = {
+        "tn_status_string": ([i32], ctypes.c_char_p),
+        "tn_last_cuda_error": ([], ctypes.c_char_p),
+        "tn_row_words": ([u64], u64),
+        "tn_kernel_launches": ([], u64),
+        "tn_init_matrix": ([vp, u32, u32, vp, vp], i32),
+        "tn_component_matrix": ([vp, vp, vp, u64, u32, vp, vp, u32, vp], i32),
+        "tn_component_columns": ([vp, vp, vp, u64, u32, vp, u32, vp, vp, u32, vp], i32),
+        "tn_out_sizes": ([vp, u32, u32, vp, vp, vp, vp], i32),
+        "tn_plan_create": ([vp, vp, vp, u64, u32, vp, vp, vp, ctypes.POINTER(vp)], i32),
+        "tn_plan_apply": ([vp, vp, u32, vp, vp, u32, vp], i32),
+        "tn_plan_apply_batch": ([vp, vp, vp, u32, u32, vp], i32),
+        "tn_plan_status": ([vp, vp], i32),
+        "tn_plan_get_stats": ([vp, ctypes.POINTER(_Stats)], i32),
+        "tn_plan_destroy": ([vp, vp], i32),
+        "tn_hash_proxy": ([vp, vp, u64, u32, u32, u32, u64, vp, vp, vp, vp], i32),
+        "tn_hash_estimate": ([vp, u32, u32, vp, u32, vp, u32, vp, vp], i32),
+        "tn_out_component_sizes_host": ([vp, vp, vp, u64, u32, vp, vp, vp], i32),
+    }
+    for name, (args, res) in sigs.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(status: int, where: str):
+    if status != TN_OK:
+        raise TnError(status, where)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(x):
+    return None if x is None else ctypes.c_void_p(x.data_ptr())
+
+
+def _dev(x, dtype_names, what):
+    torch = _torch()
+    if not isinstance(x, torch.Tensor) or not x.is_cuda:
+        raise TypeError(f"{what} must be a CUDA tensor")
+    if not x.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    if str(x.dtype).replace("torch.", "") not in dtype_names:
+        raise TypeError(f"{what} has dtype {x.dtype}, expected one of {dtype_names}")
+    return x
+
+
+def tn_row_words(ncols: int) -> int:
+    return int(load_library().tn_row_words(ncols))
+
+
+def tn_kernel_launches() -> int:
+    """Kernels launched by libtn in this process so far."""
+    return int(load_library().tn_kernel_launches())
+
+
+def tn_init_matrix(S, n_rows: int, ncols: int | None = None, src=None, stream=None):
+    """Initial state of Algorithm 1: identity, or the listed source columns."""
+    lib = load_library()
+    ncols = n_rows if ncols is None else ncols
+    S = _matrix(S, n_rows, ncols, S.device)
+    _check(lib.tn_init_matrix(_ptr(S), n_rows, ncols, _ptr(src), _stream(stream)), "tn_init_matrix")
+    return S
+
+
+def tn_status_string(status: int) -> str:
+    return load_library().tn_status_string(status).decode()
+
+
+def _events(u, v, t):
+    _dev(u, ("int32", "uint32"), "u")
+    _dev(v, ("int32", "uint32"), "v")
+    _dev(t, ("int64",), "t")
+    if not (u.numel() == v.numel() == t.numel()):
+        raise ValueError("u, v, t must have the same length")
+    return u.numel()
+
+
+def _matrix(S, n_rows, ncols, device):
+    torch = _torch()
+    shape = (n_rows, tn_row_words(ncols))
+    if S is None:
+        return torch.empty(shape, dtype=torch.int64, device=device)
+    _dev(S, ("int64", "uint64"), "S")
+    if tuple(S.shape) != shape:
+        raise ValueError(f"S must have shape {shape}")
+    return S
+
+
+def tn_component_matrix(u, v, t, n: int, S=None, t_last=None, init: bool = True, stream=None):
+    """Algorithm 1 (Section 3.1) over one event batch; returns S (int64 [n, W])."""
+    lib = load_library()
+    m = _events(u, v, t)
+    S = _matrix(S, n, n, u.device)
+    if t_last is not None:
+        _dev(t_last, ("int64",), "t_last")
+    _check(lib.tn_component_matrix(_ptr(u), _ptr(v), _ptr(t), m, n, _ptr(S), _ptr(t_last),
+                                   TN_INIT_IDENTITY if init else 0, _stream(stream)), "tn_component_matrix")
+    return S
+
+
+def tn_component_columns(u, v, t, n: int, src, S=None, t_last=None, init: bool = True, stream=None):
+    """Out-components of the listed sources only (column c = source src[c])."""
+    lib = load_library()
+    m = _events(u, v, t)
+    _dev(src, ("int32", "uint32"), "src")
+    S = _matrix(S, n, src.numel(), u.device)
+    _check(lib.tn_component_columns(_ptr(u), _ptr(v), _ptr(t), m, n, _ptr(src), src.numel(), _ptr(S),
+                                    _ptr(t_last), TN_INIT_IDENTITY if init else 0, _stream(stream)),
+           "tn_component_columns")
+    return S
+
+
+def tn_out_sizes(S, n_rows: int, ncols: int, in_sizes: bool = False, argmax: bool = False, stream=None):
+    """Column (out-component) and row (in-component) sizes; returns
+    (out int32[ncols], in int32[n_rows] or None, argmax int32[1] or None)."""
+    torch = _torch()
+    lib = load_library()
+    S = _matrix(S, n_rows, ncols, S.device)
+    out = torch.empty(ncols, dtype=torch.int32, device=S.device)
+    ins = torch.empty(n_rows, dtype=torch.int32, device=S.device) if in_sizes else None
+    am = torch.empty(1, dtype=torch.int32, device=S.device) if argmax else None
+    _check(lib.tn_out_sizes(_ptr(S), n_rows, ncols, _ptr(out), _ptr(ins), _ptr(am), _stream(stream)),
+           "tn_out_sizes")
+    return out, ins, am
+
+
+def tn_hash_proxy(u, v, n: int, k: int, R: int, seed: int, events: bool = True, stream=None):
+    """Hash tables H (int32 [R, n]) and super-events (pu, pv: int32 [R, m])."""
+    torch = _torch()
+    lib = load_library()
+    device = u.device if u is not None else torch.device("cuda")
+    H = torch.empty((R, n), dtype=torch.int32, device=device)
+    pu = pv = None
+    m = 0
+    if events and u is not None:
+        m = u.numel()
+        _dev(u, ("int32", "uint32"), "u")
+        _dev(v, ("int32", "uint32"), "v")
+        pu = torch.empty((R, m), dtype=torch.int32, device=device)
+        pv = torch.empty((R, m), dtype=torch.int32, device=device)
+    _check(lib.tn_hash_proxy(_ptr(u) if m else None, _ptr(v) if m else None, m, n, k, R, seed & (2**64 - 1),
+                             _ptr(H), _ptr(pu), _ptr(pv), _stream(stream)), "tn_hash_proxy")
+    return H, pu, pv
+
+
+def tn_hash_estimate(P, R: int, k: int, H, n: int, src=None, stream=None):
+    """Fusion by intersection (Section 4.2); est int32[nsrc]."""
+    torch = _torch()
+    lib = load_library()
+    _dev(P, ("int64", "uint64"), "P")
+    _dev(H, ("int32", "uint32"), "H")
+    nsrc = n if src is None else src.numel()
+    if src is not None:
+        _dev(src, ("int32", "uint32"), "src")
+    est = torch.empty(nsrc, dtype=torch.int32, device=P.device)
+    _check(lib.tn_hash_estimate(_ptr(P), R, k, _ptr(H), n, _ptr(src), nsrc, _ptr(est), _stream(stream)),
+           "tn_hash_estimate")
+    return est
+
+
+def tn_out_component_sizes_host(u, v, t, n: int):
+    """Whole exact path from host numpy arrays; returns (sizes uint32[n], argmax)."""
+    import numpy as np
+    lib = load_library()
+    u = np.ascontiguousarray(u, dtype=np.uint32)
+    v = np.ascontiguousarray(v, dtype=np.uint32)
+    t = np.ascontiguousarray(t, dtype=np.int64)
+    out = np.empty(n, dtype=np.uint32)
+    am = np.zeros(1, dtype=np.uint32)
+    _check(lib.tn_out_component_sizes_host(u.ctypes.data, v.ctypes.data, t.ctypes.data, len(u), n,
+                                           out.ctypes.data, am.ctypes.data, _stream()),
+           "tn_out_component_sizes_host")
+    return out, int(am[0])
+
+
+def tn_out_component_sizes_host_ptrs(u_ptr: int, v_ptr: int, t_ptr: int, m: int, n: int, out_ptr: int,
+                                     argmax_ptr: int | None = None, stream=None):
+    """Same as ``tn_out_component_sizes_host`` on raw host pointers (pinned buffers)."""
+    lib = load_library()
+    _check(lib.tn_out_component_sizes_host(u_ptr, v_ptr, t_ptr, m, n, out_ptr, argmax_ptr, _stream(stream)),
+           "tn_out_component_sizes_host")
+
+
+class Plan:
+    """A validated, scheduled event batch (tn_plan_create / tn_plan_apply)."""
+
+    def __init__(self, u, v, t, n: int, t_after=None, window_events: int = 0, slab_words: int = 0,
+                 stream=None):
+        lib = load_library()
+        self.m = _events(u, v, t)
+        self.n = n
+        opt = _Options(window_events, slab_words)
+        h = ctypes.c_void_p()
+        if t_after is not None:
+            _dev(t_after, ("int64",), "t_after")
+        _check(lib.tn_plan_create(_ptr(u), _ptr(v), _ptr(t), self.m, n, _ptr(t_after), ctypes.byref(opt),
+                                  _stream(stream), ctypes.byref(h)), "tn_plan_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def apply(self, S, ncols: int | None = None, src=None, t_last=None, init: bool = False, stream=None):
+        lib = load_library()
+        ncols = self.n if ncols is None else ncols
+        S = _matrix(S, self.n, ncols, S.device if S is not None else None)
+        _check(lib.tn_plan_apply(self._h, _ptr(S), ncols, _ptr(src), _ptr(t_last),
+                                 TN_INIT_IDENTITY if init else 0, _stream(stream)), "tn_plan_apply")
+        return S
+
+    def status(self, stream=None) -> int:
+        return int(load_library().tn_plan_status(self._h, _stream(stream)))
+
+    def stats(self) -> dict:
+        st = _Stats()
+        _check(load_library().tn_plan_get_stats(self._h, ctypes.byref(st)), "tn_plan_get_stats")
+        return {f: getattr(st, f) for f, _ in _Stats._fields_}
+
+    def destroy(self, stream=None):
+        if self._h:
+            load_library().tn_plan_destroy(self._h, _stream(stream))
+            self._h = None
+
+    def __del__(self):
+        try:
+            if self._h and _lib is not None:
+                _lib.tn_plan_destroy(self._h, None)
+                self._h = None
+        except Exception:
+            pass
+
+
+def tn_plan_apply_batch(plans, mats, ncols=None, init: bool = True, stream=None):
+    """One launch over several (plan, matrix) pairs."""
+    lib = load_library()
+    count = len(plans)
+    ncols = ncols or [p.n for p in plans]
+    hp = (ctypes.c_void_p * count)(*[p.handle for p in plans])
+    hs = (ctypes.c_void_p * count)(*[m.data_ptr() for m in mats])
+    hn = (ctypes.c_uint32 * count)(*ncols)
+    _check(lib.tn_plan_apply_batch(hp, hs, hn, count, TN_INIT_IDENTITY if init else 0, _stream(stream)),
+           "tn_plan_apply_batch")
+    return mats

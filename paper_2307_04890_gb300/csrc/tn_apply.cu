@@ -1,0 +1,517 @@
+// Column-slab streaming of a scheduled event batch into component matrices.
+//
+// Algorithm 1 (Section 3.1) updates whole rows, but bit column j of the matrix
+// (the out-component of source j) evolves independently of every other column.
+// Each CTA therefore owns a slab of `sw` consecutive 64-bit words of every row
+// (64*sw source columns) and streams the whole level-ordered schedule over it:
+//   * a producer warp copies the schedule, tile by tile, into a ring of shared
+//     memory stages with bulk asynchronous copies (cp.async.bulk, completion on
+//     an mbarrier), so the ops are read from L2/HBM once per CTA and without
+//     occupying the consumer threads;
+//   * eight consumer warps apply a tile: for each op, 128-bit loads of the two
+//     row segments, OR, 128-bit stores (four ops in flight per thread); the
+//     per-tile named barrier orders one level's stores before the next level's
+//     loads.
+// All waits are bounded (TN_ETIMEOUT).  The per-tile barrier is a reduction
+// (bar.red.or) of every consumer's stop condition, so all consumers leave the
+// loop at the same barrier and none can be left waiting on it.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "tn_internal.cuh"
+
+namespace tn {
+
+constexpr int kConsumerWarps = 8;
+constexpr int kConsumers = 32 * kConsumerWarps;
+constexpr int kThreads = kConsumers + 32;
+constexpr int kStages = 4;
+constexpr uint32_t kTileOps = 2048;
+constexpr uint32_t kStageOps = kTileOps + 2;
+constexpr uint32_t kEndTile = 0xFFFFFFFFu;
+constexpr int kMaxJobs = 24;
+
+struct Job {
+    const uint2 *ops;
+    const uint32_t *lvl;
+    const uint32_t *aux;
+    uint64_t nlev;
+    uint64_t *S;
+    uint64_t ld;    // row stride in words
+    uint64_t *tmp;  // saved-row slots, ld words each
+    int32_t *status;
+    uint32_t sw;    // slab words per CTA (power of two >= 2)
+    uint32_t lsw;   // log2(sw)
+    uint32_t cta_begin;
+    uint32_t pad;
+};
+
+struct JobList {
+    Job job[kMaxJobs];
+    uint32_t count;
+};
+
+struct TileHdr {
+    uint32_t count;  // ops in the tile, kEndTile = no more tiles
+    uint32_t off;    // first op's index inside the stage buffer (0 or 1)
+};
+
+__device__ inline uint32_t find_job(const JobList &jl, uint32_t cta)
+{
+    uint32_t j = 0;
+    while (j + 1 < jl.count && jl.job[j + 1].cta_begin <= cta) ++j;
+    return j;
+}
+
+__device__ inline uint64_t *row_ptr(const Job &J, uint32_t ref, uint64_t col)
+{
+    if (ref & kTempRef) return J.tmp + (uint64_t)(ref & ~kTempRef) * J.ld + col;
+    return J.S + (uint64_t)ref * J.ld + col;
+}
+
+// PULL: S[x] |= OR of the listed source rows (aux[b] = count, then refs)
+__device__ inline void apply_pull(const Job &J, uint32_t x, uint32_t b, uint64_t col)
+{
+    uint64_t *pd = J.S + (uint64_t)x * J.ld + col;
+    u64x2 acc = ld_row16(pd);
+    const uint32_t c = __ldg(J.aux + b);
+    for (uint32_t i = 0; i < c; i += 8) {
+        uint32_t ref[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) ref[k] = (i + k < c) ? __ldg(J.aux + b + 1 + i + k) : kNoRef;
+        u64x2 r[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            r[k] = (ref[k] != kNoRef) ? ld_row16(row_ptr(J, ref[k], col)) : u64x2{0, 0};
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc = or16(acc, r[k]);
+    }
+    st_row16(pd, acc);
+}
+
+__device__ inline void apply_tile(const Job &J, const uint2 *ops, uint32_t count, uint32_t ct, uint64_t w0)
+{
+    const uint32_t cpr_log = J.lsw - 1;  // 16-byte chunks per row segment = sw/2
+    const uint32_t chunk = ct & ((1u << cpr_log) - 1u);
+    const uint64_t col = w0 + 2ull * chunk;
+    if (col >= J.ld) return;  // partial last slab
+    const uint32_t stride = (uint32_t)kConsumers >> cpr_log;
+    for (uint32_t o = ct >> cpr_log; o < count; o += 4 * stride) {
+        uint2 op[4];
+        bool live[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t idx = o + k * stride;
+            live[k] = idx < count;
+            op[k] = live[k] ? ops[idx] : make_uint2(0u, 0u);
+        }
+        // loads of all four ops first (they are independent inside a level)
+        u64x2 ra[4], rb[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t kind = op[k].x >> kKindShift;
+            if (!live[k] || kind == kPull) continue;
+            if (kind != kCopy) ra[k] = ld_row16(J.S + (uint64_t)(op[k].x & kIdMask) * J.ld + col);
+            rb[k] = ld_row16(J.S + (uint64_t)op[k].y * J.ld + col);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t kind = op[k].x >> kKindShift;
+            if (!live[k] || kind == kPull) continue;
+            const uint64_t ia = (uint64_t)(op[k].x & kIdMask) * J.ld + col;
+            if (kind == kCopy) {
+                st_row16(J.tmp + ia, rb[k]);
+            } else {
+                const u64x2 r = or16(ra[k], rb[k]);
+                st_row16(J.S + ia, r);
+                if (kind == kEvent) st_row16(J.S + (uint64_t)op[k].y * J.ld + col, r);
+            }
+        }
+    }
+    // multi-source updates of tie groups (hub rows) in a second pass
+    for (uint32_t o = ct >> cpr_log; o < count; o += stride) {
+        const uint2 op = ops[o];
+        if ((op.x >> kKindShift) == kPull) apply_pull(J, op.x & kIdMask, op.y, col);
+    }
+}
+
+// Barrier of the consumer warps (named barrier 1) that also ORs a predicate
+// across them, so that every consumer takes the same decision to stop.
+__device__ inline bool consumers_sync_or(bool p)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred ip, op;\n\t"
+        "setp.ne.u32 ip, %1, 0;\n\t"
+        "bar.red.or.pred op, 1, %2, ip;\n\t"
+        "selp.u32 %0, 1, 0, op;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)p), "r"(kConsumers)
+        : "memory");
+    return r != 0;
+}
+
+__global__ void __launch_bounds__(kThreads, 2) stream_kernel(const __grid_constant__ JobList jl)
+{
+    extern __shared__ __align__(128) uint8_t smem[];
+    uint2 *stage_ops = reinterpret_cast<uint2 *>(smem);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + sizeof(uint2) * kStages * kStageOps);
+    uint64_t *empty = full + kStages;
+    TileHdr *hdr = reinterpret_cast<TileHdr *>(empty + kStages);
+    __shared__ uint32_t producer_abort;
+    __shared__ int32_t gate;
+
+    const Job &J = jl.job[find_job(jl, blockIdx.x)];
+    const uint64_t w0 = (uint64_t)(blockIdx.x - J.cta_begin) << J.lsw;
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+    if (threadIdx.x == 0) {
+        gate = *(volatile int32_t *)J.status;  // an earlier error gates this job
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kConsumerWarps);
+        }
+        producer_abort = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (gate != 0) return;
+
+    if (warp == 0) {
+        // ---------------- producer ----------------
+        uint64_t tile = 0;
+        int ok = 1;
+        for (uint64_t l0 = 0; l0 < J.nlev && ok; l0 += 32) {
+            const uint64_t l = l0 + lane;
+            const uint32_t beg = l < J.nlev ? __ldg(J.lvl + l) : 0u;
+            const uint32_t end = l < J.nlev ? __ldg(J.lvl + l + 1) : 0u;
+            const uint32_t nl = (J.nlev - l0 < 32) ? (uint32_t)(J.nlev - l0) : 32u;
+            for (uint32_t k = 0; k < nl && ok; ++k) {
+                const uint32_t b = __shfl_sync(0xffffffffu, beg, k);
+                const uint32_t e = __shfl_sync(0xffffffffu, end, k);
+                for (uint32_t c = b; c < e && ok; c += kTileOps) {
+                    const uint32_t ce = min(e, c + kTileOps);
+                    const int s = (int)(tile % kStages);
+                    if (lane == 0) {
+                        if (tile >= kStages && !mbar_wait_bounded(&empty[s], (uint32_t)((tile / kStages) - 1) & 1u)) {
+                            record_status(J.status, TN_ETIMEOUT);
+                            producer_abort = 1;
+                            ok = 0;
+                        } else {
+                            const uint32_t a0 = c & ~1u;
+                            const uint32_t bytes = ((ce - a0 + 1u) & ~1u) * (uint32_t)sizeof(uint2);
+                            hdr[s].count = ce - c;
+                            hdr[s].off = c - a0;
+                            mbar_arrive_expect_tx(&full[s], bytes);
+                            bulk_g2s(stage_ops + (size_t)s * kStageOps, J.ops + a0, bytes, &full[s]);
+                        }
+                    }
+                    ok = __shfl_sync(0xffffffffu, ok, 0);
+                    if (ok) ++tile;
+                }
+            }
+        }
+        if (lane == 0) {
+            if (ok) {
+                const int s = (int)(tile % kStages);
+                if (tile >= kStages && !mbar_wait_bounded(&empty[s], (uint32_t)((tile / kStages) - 1) & 1u)) {
+                    record_status(J.status, TN_ETIMEOUT);
+                    producer_abort = 1;
+                } else {
+                    hdr[s].count = kEndTile;
+                    hdr[s].off = 0;
+                    mbar_arrive(&full[s]);
+                    ++tile;
+                }
+            }
+            // no bulk copy may still be writing this CTA's shared memory at exit
+            const uint64_t first = tile > (uint64_t)kStages ? tile - kStages : 0;
+            for (uint64_t q = first; q < tile; ++q)
+                mbar_wait_bounded(&full[q % kStages], (uint32_t)(q / kStages) & 1u);
+        }
+    } else {
+        // ---------------- consumers ----------------
+        const uint32_t ct = threadIdx.x - 32;
+        for (uint64_t tile = 0;; ++tile) {
+            const int s = (int)(tile % kStages);
+            const uint32_t par = (uint32_t)(tile / kStages) & 1u;
+            const bool ready = mbar_wait_bounded(&full[s], par);
+            if (!ready && ct == 0) record_status(J.status, TN_ETIMEOUT);
+            const bool stop = !ready || *(volatile uint32_t *)&producer_abort != 0 ||
+                              (ready && hdr[s].count == kEndTile);
+            // level barrier: the previous tile's stores are ordered before this
+            // tile's loads, and all consumers agree on stopping
+            if (consumers_sync_or(stop)) break;
+            apply_tile(J, stage_ops + (size_t)s * kStageOps + hdr[s].off, hdr[s].count, ct, w0);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);
+        }
+    }
+}
+
+// S <- identity (full matrix) -- Algorithm 1, first line; one row per warp step
+__global__ void init_identity_kernel(uint64_t *S, uint32_t n_rows, uint64_t ld, const int32_t *status)
+{
+    if (*(volatile const int32_t *)status != 0) return;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    for (uint64_t r = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); r < n_rows; r += warps) {
+        uint64_t *row = S + r * ld;
+        const uint64_t diag = r >> 6;
+        for (uint64_t w = 2 * lane; w < ld; w += 64) {
+            u64x2 z{w == diag ? (1ull << (r & 63)) : 0ull, w + 1 == diag ? (1ull << (r & 63)) : 0ull};
+            st_row16(row + w, z);
+        }
+    }
+}
+
+__global__ void zero_kernel(uint64_t *S, uint64_t total, const int32_t *status)
+{
+    if (*(volatile const int32_t *)status != 0) return;
+    for (uint64_t i = 2 * (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x); i < total;
+         i += 2 * (uint64_t)gridDim.x * blockDim.x)
+        st_row16(S + i, u64x2{0ull, 0ull});
+}
+
+// column c of the matrix starts as the single source src[c]; ids >= n_rows
+// are skipped and reported as TN_ERANGE
+__global__ void init_sources_kernel(uint64_t *S, uint64_t ld, const uint32_t *src, uint32_t nsrc, uint32_t n_rows,
+                                    int32_t *status)
+{
+    if (*(volatile const int32_t *)status != 0) return;
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < nsrc; c += gridDim.x * blockDim.x) {
+        const uint32_t x = src[c];
+        if (x >= n_rows) {
+            record_status(status, TN_ERANGE);
+            continue;
+        }
+        atomicOr((unsigned long long *)(S + (uint64_t)x * ld + (c >> 6)), 1ull << (c & 63));
+    }
+}
+
+__global__ void check_ids_kernel(const uint32_t *ids, uint32_t count, uint32_t n, int32_t *status)
+{
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
+        if (ids[i] >= n) record_status(status, TN_ERANGE);
+}
+
+// Validating check that every source id is a node id (< n).
+static tn_status validate_sources(const uint32_t *src, uint32_t nsrc, uint32_t n, cudaStream_t st)
+{
+    int32_t *d = nullptr, h = 0;
+    TN_CUDA_TRY(cudaMallocAsync((void **)&d, sizeof(int32_t), st));
+    TN_CUDA_TRY(cudaMemsetAsync(d, 0, sizeof(int32_t), st));
+    tn_internal_count_launches(1);
+    check_ids_kernel<<<(nsrc + 255) / 256 < 1024 ? (nsrc + 255) / 256 : 1024, 256, 0, st>>>(src, nsrc, n, d);
+    TN_CUDA_TRY(cudaGetLastError());
+    TN_CUDA_TRY(cudaMemcpyAsync(&h, d, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    TN_CUDA_TRY(cudaFreeAsync(d, st));
+    TN_CUDA_TRY(cudaStreamSynchronize(st));
+    return (tn_status)h;
+}
+
+// batch order check (streaming, Section 3.5): the batch must start after t_last
+__global__ void order_gate_kernel(const int64_t *tb, const int64_t *t_last, int32_t *status)
+{
+    if (*t_last >= tb[0]) record_status(status, TN_EORDER);
+}
+
+__global__ void set_t_last_kernel(const int64_t *tb, int64_t *t_last, const int32_t *status)
+{
+    if (*(volatile const int32_t *)status == 0) *t_last = tb[1];
+}
+
+static int grid_for(uint64_t work)
+{
+    uint64_t g = (work + 255) / 256;
+    return (int)(g < 1 ? 1 : (g > 8192 ? 8192 : g));
+}
+
+static uint32_t log2u(uint32_t x)
+{
+    uint32_t l = 0;
+    while ((1u << l) < x) ++l;
+    return l;
+}
+
+tn_status apply_jobs(const tn_plan *const *plans, uint64_t *const *S, const uint32_t *ncols,
+                     const uint32_t *const *src, int64_t *const *t_last, uint32_t count, uint32_t flags,
+                     cudaStream_t st)
+{
+    // host-side argument checks
+    for (uint32_t i = 0; i < count; ++i) {
+        const tn_plan *p = plans[i];
+        if (!p || !S[i] || ncols[i] == 0) return TN_EINVAL;
+        // the identity initialisation needs one column per node
+        if ((flags & TN_INIT_IDENTITY) && !src[i] && ncols[i] != p->n) return TN_EINVAL;
+    }
+    static bool attr_set = false;
+    const size_t smem = sizeof(uint2) * kStages * kStageOps + 2 * kStages * sizeof(uint64_t) + kStages * sizeof(TileHdr);
+    if (!attr_set) {
+        TN_CUDA_TRY(cudaFuncSetAttribute(stream_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr_set = true;
+    }
+    uint64_t *tmps[kMaxJobs];
+    for (uint32_t base = 0; base < count; base += kMaxJobs) {
+        const uint32_t nj = count - base < (uint32_t)kMaxJobs ? count - base : (uint32_t)kMaxJobs;
+        JobList jl;
+        memset(&jl, 0, sizeof(jl));
+        jl.count = nj;
+        uint32_t ctas = 0;
+        for (uint32_t j = 0; j < nj; ++j) {
+            const uint32_t i = base + j;
+            const tn_plan *p = plans[i];
+            const uint64_t ld = tn_row_words(ncols[i]);
+            tmps[j] = nullptr;
+            if (t_last && t_last[i]) {
+                tn_internal_count_launches(1);
+                order_gate_kernel<<<1, 1, 0, st>>>(p->d_tbounds, t_last[i], p->d_status);
+            }
+            if (flags & TN_INIT_IDENTITY) {
+                if (!src[i]) {
+                    tn_internal_count_launches(1);
+                    init_identity_kernel<<<grid_for(p->n * 32ull), 256, 0, st>>>(S[i], p->n, ld, p->d_status);
+                } else {
+                    tn_internal_count_launches(1);
+                    zero_kernel<<<grid_for(p->n * ld / 2), 256, 0, st>>>(S[i], (uint64_t)p->n * ld, p->d_status);
+                    tn_internal_count_launches(1);
+                    init_sources_kernel<<<grid_for(ncols[i]), 256, 0, st>>>(S[i], ld, src[i], ncols[i], p->n,
+                                                                            p->d_status);
+                }
+            }
+            if (p->temps) TN_CUDA_TRY(cudaMallocAsync((void **)&tmps[j], p->temps * ld * sizeof(uint64_t), st));
+            uint32_t sw = p->slab_words ? p->slab_words : 4u;
+            while ((uint64_t)sw > ld && sw > 2) sw >>= 1;
+            Job &J = jl.job[j];
+            J.ops = p->d_ops;
+            J.lvl = p->d_lvl;
+            J.aux = p->d_aux;
+            J.nlev = p->levels;
+            J.S = S[i];
+            J.ld = ld;
+            J.tmp = tmps[j];
+            J.status = p->d_status;
+            J.sw = sw;
+            J.lsw = log2u(sw);
+            J.cta_begin = ctas;
+            ctas += (uint32_t)((ld + sw - 1) / sw);
+        }
+        TN_CUDA_TRY(cudaGetLastError());
+        if (ctas) {
+            tn_internal_count_launches(1);
+            stream_kernel<<<ctas, kThreads, smem, st>>>(jl);
+        }
+        TN_CUDA_TRY(cudaGetLastError());
+        for (uint32_t j = 0; j < nj; ++j) {
+            const uint32_t i = base + j;
+            if (t_last && t_last[i]) {
+                tn_internal_count_launches(1);
+                set_t_last_kernel<<<1, 1, 0, st>>>(plans[i]->d_tbounds, t_last[i], plans[i]->d_status);
+            }
+            if (tmps[j]) TN_CUDA_TRY(cudaFreeAsync(tmps[j], st));
+        }
+        TN_CUDA_TRY(cudaGetLastError());
+    }
+    return TN_OK;
+}
+
+}  // namespace tn
+
+using namespace tn;
+
+extern "C" tn_status tn_plan_apply(const tn_plan *plan, uint64_t *S, uint32_t ncols, const uint32_t *src,
+                                   int64_t *t_last, uint32_t flags, void *stream)
+{
+    if (!plan || !S || (flags & ~TN_INIT_IDENTITY)) return TN_EINVAL;
+    return apply_jobs(&plan, &S, &ncols, &src, &t_last, 1, flags, (cudaStream_t)stream);
+}
+
+extern "C" tn_status tn_plan_apply_batch(const tn_plan *const *plans, uint64_t *const *S, const uint32_t *ncols,
+                                         uint32_t count, uint32_t flags, void *stream)
+{
+    if (!plans || !S || !ncols || count == 0 || (flags & ~TN_INIT_IDENTITY)) return TN_EINVAL;
+    const uint32_t **src = (const uint32_t **)calloc(count, sizeof(uint32_t *));
+    if (!src) return TN_ENOMEM;
+    tn_status rc = apply_jobs(plans, S, ncols, src, nullptr, count, flags, (cudaStream_t)stream);
+    free(src);
+    return rc;
+}
+
+static tn_status one_shot(const uint32_t *u, const uint32_t *v, const int64_t *t, uint64_t m, uint32_t n,
+                          const uint32_t *src, uint32_t ncols, uint64_t *S, int64_t *t_last, uint32_t flags,
+                          void *stream)
+{
+    if (!S || n == 0 || n >= (1u << 30) || (flags & ~TN_INIT_IDENTITY)) return TN_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const uint64_t ld = tn_row_words(ncols);
+    if (src && (flags & TN_INIT_IDENTITY)) {
+        const tn_status rc = validate_sources(src, ncols, n, st);
+        if (rc != TN_OK) return rc;
+    }
+    if (m == 0) {
+        if (flags & TN_INIT_IDENTITY) {
+            int32_t *zero = nullptr;
+            TN_CUDA_TRY(cudaMallocAsync((void **)&zero, sizeof(int32_t), st));
+            TN_CUDA_TRY(cudaMemsetAsync(zero, 0, sizeof(int32_t), st));
+            if (!src) {
+                tn_internal_count_launches(1);
+                init_identity_kernel<<<grid_for(n * 32ull), 256, 0, st>>>(S, n, ld, zero);
+            } else {
+                tn_internal_count_launches(1);
+                zero_kernel<<<grid_for(n * ld / 2), 256, 0, st>>>(S, (uint64_t)n * ld, zero);
+                tn_internal_count_launches(1);
+                init_sources_kernel<<<grid_for(ncols), 256, 0, st>>>(S, ld, src, ncols, n, zero);
+            }
+            TN_CUDA_TRY(cudaFreeAsync(zero, st));
+            TN_CUDA_TRY(cudaGetLastError());
+        }
+        return TN_OK;
+    }
+    tn_plan *plan = nullptr;
+    tn_status rc = tn_plan_create(u, v, t, m, n, t_last, nullptr, stream, &plan);
+    if (rc != TN_OK) return rc;
+    rc = apply_jobs((const tn_plan *const *)&plan, &S, &ncols, &src, &t_last, 1, flags, st);
+    tn_plan_destroy(plan, stream);
+    return rc;
+}
+
+extern "C" tn_status tn_component_matrix(const uint32_t *u, const uint32_t *v, const int64_t *t, uint64_t m,
+                                         uint32_t n, uint64_t *S, int64_t *t_last, uint32_t flags, void *stream)
+{
+    return one_shot(u, v, t, m, n, nullptr, n, S, t_last, flags, stream);
+}
+
+extern "C" tn_status tn_component_columns(const uint32_t *u, const uint32_t *v, const int64_t *t, uint64_t m,
+                                          uint32_t n, const uint32_t *src, uint32_t nsrc, uint64_t *S,
+                                          int64_t *t_last, uint32_t flags, void *stream)
+{
+    if (!src || nsrc == 0) return TN_EINVAL;
+    return one_shot(u, v, t, m, n, src, nsrc, S, t_last, flags, stream);
+}
+
+extern "C" tn_status tn_init_matrix(uint64_t *S, uint32_t n_rows, uint32_t ncols, const uint32_t *src, void *stream)
+{
+    if (!S || n_rows == 0 || ncols == 0 || n_rows >= (1u << 30)) return TN_EINVAL;
+    if (!src && ncols != n_rows) return TN_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (src) {
+        const tn_status rc = validate_sources(src, ncols, n_rows, st);
+        if (rc != TN_OK) return rc;
+    }
+    const uint64_t ld = tn_row_words(ncols);
+    int32_t *zero = nullptr;
+    TN_CUDA_TRY(cudaMallocAsync((void **)&zero, sizeof(int32_t), st));
+    TN_CUDA_TRY(cudaMemsetAsync(zero, 0, sizeof(int32_t), st));
+    if (!src) {
+        tn_internal_count_launches(1);
+        init_identity_kernel<<<grid_for(n_rows * 32ull), 256, 0, st>>>(S, n_rows, ld, zero);
+    } else {
+        tn_internal_count_launches(2);
+        zero_kernel<<<grid_for(n_rows * ld / 2), 256, 0, st>>>(S, (uint64_t)n_rows * ld, zero);
+        init_sources_kernel<<<grid_for(ncols), 256, 0, st>>>(S, ld, src, ncols, n_rows, zero);
+    }
+    TN_CUDA_TRY(cudaGetLastError());
+    TN_CUDA_TRY(cudaFreeAsync(zero, st));
+    return TN_OK;
+}

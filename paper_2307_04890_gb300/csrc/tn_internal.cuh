@@ -1,0 +1,209 @@
+// Internal helpers shared by the libtn translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tn.h"
+
+#define TN_CUDA_TRY(expr)                                   \
+    do {                                                    \
+        cudaError_t err_ = (expr);                          \
+        if (err_ != cudaSuccess) {                          \
+            tn_internal_set_cuda_error(err_);               \
+            return err_ == cudaErrorMemoryAllocation ? TN_ENOMEM : TN_ECUDA; \
+        }                                                   \
+    } while (0)
+
+void tn_internal_set_cuda_error(cudaError_t err);
+// Keeps memory freed to the current device's stream-ordered pool cached for
+// reuse instead of returning it to the driver at every synchronisation.
+void tn_internal_keep_pool(void);
+// Adds `count` to the process-wide kernel launch counter (tn_kernel_launches).
+void tn_internal_count_launches(uint64_t count);
+
+namespace tn {
+
+// Bounded device-side waits: a wait that has not completed after this many
+// polls (each poll suspends for up to ~1 us) records TN_ETIMEOUT and gives up.
+constexpr uint32_t kWaitPolls = 1u << 22;
+
+// Op encoding of the row-update schedule (see tn_plan.cu).
+//   a: bits 31..30 = kind, bits 29..0 = destination node / temp id
+//   b: EVENT / ONEWAY / COPY: source node id;  PULL: index into the aux list
+// aux list of a PULL at index b: aux[b] = count c, aux[b+1 .. b+c] = source
+// references (bit 31 set = temp slot, else node id).
+enum OpKind : uint32_t { kEvent = 0u, kOneway = 1u, kCopy = 2u, kPull = 3u };
+constexpr uint32_t kKindShift = 30;
+constexpr uint32_t kIdMask = (1u << 30) - 1u;
+constexpr uint32_t kTempRef = 1u << 31;
+constexpr uint32_t kNoRef = 0xFFFFFFFFu;  // empty slot in a batch of source references
+
+__host__ __device__ inline uint32_t op_a(uint32_t kind, uint32_t id) { return (kind << kKindShift) | id; }
+
+__device__ inline void record_status(int32_t *status, int32_t code)
+{
+    if (status) atomicCAS(status, 0, code);
+}
+
+// ---------------------------------------------------------------------------
+// mbarrier and bulk-copy (TMA, non-tensor) PTX wrappers
+// ---------------------------------------------------------------------------
+__device__ inline uint32_t smem_addr(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ inline void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ inline void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ inline void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ inline void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
+                     smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// One poll: true once the phase with the given parity has completed.
+__device__ inline bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(1000u)
+        : "memory");
+    return done != 0;
+}
+
+// Bounded wait; returns false on timeout.
+__device__ inline bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+{
+    for (uint32_t i = 0; i < kWaitPolls; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// Bulk global -> shared copy of `bytes` (multiple of 16, both addresses
+// 16-byte aligned), completion signalled on `bar` as transaction bytes.
+__device__ inline void bulk_g2s(void *smem_dst, const void *gmem_src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(smem_dst)),
+        "l"(gmem_src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// 128-bit row-segment access (L2-cached, not allocated in L1)
+// ---------------------------------------------------------------------------
+struct u64x2 {
+    uint64_t x, y;
+};
+
+__device__ inline u64x2 ld_row16(const uint64_t *p)
+{
+    u64x2 r;
+    asm volatile("ld.global.cg.v2.u64 {%0, %1}, [%2];" : "=l"(r.x), "=l"(r.y) : "l"(p) : "memory");
+    return r;
+}
+
+__device__ inline void st_row16(uint64_t *p, u64x2 r)
+{
+    asm volatile("st.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(r.x), "l"(r.y) : "memory");
+}
+
+__device__ inline u64x2 or16(u64x2 a, u64x2 b) { return u64x2{a.x | b.x, a.y | b.y}; }
+
+// ---------------------------------------------------------------------------
+// Block-wide exclusive scan of an array (generic pointer: shared or global).
+// All threads of the block must call it; returns the total.  `warp_sums` must
+// hold 32 entries of shared memory.
+// ---------------------------------------------------------------------------
+__device__ inline uint32_t warp_incl_scan(uint32_t x)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= (uint32_t)d) x += y;
+    }
+    return x;
+}
+
+__device__ inline uint32_t block_excl_scan_value(uint32_t x, uint32_t *warp_sums, uint32_t *total)
+{
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint32_t nwarps = (blockDim.x + 31u) >> 5;
+    uint32_t incl = warp_incl_scan(x);
+    if (lane == 31u) warp_sums[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t s = lane < nwarps ? warp_sums[lane] : 0u;
+        uint32_t si = warp_incl_scan(s);
+        if (lane < nwarps) warp_sums[lane] = si - s;
+        if (lane == nwarps - 1u) *total = si;
+    }
+    __syncthreads();
+    uint32_t r = warp_sums[warp] + incl - x;
+    __syncthreads();
+    return r;
+}
+
+__device__ inline uint32_t block_excl_scan_array(uint32_t *a, uint32_t len, uint32_t *warp_sums, uint32_t *total)
+{
+    const uint32_t per = (len + blockDim.x - 1u) / blockDim.x;
+    const uint32_t b = threadIdx.x * per;
+    const uint32_t e = min(len, b + per);
+    uint32_t sum = 0;
+    for (uint32_t i = b; i < e; ++i) sum += a[i];
+    uint32_t off = block_excl_scan_value(sum, warp_sums, total);
+    for (uint32_t i = b; i < e; ++i) {
+        uint32_t x = a[i];
+        a[i] = off;
+        off += x;
+    }
+    __syncthreads();
+    return *total;
+}
+
+}  // namespace tn
+
+// Plan object (opaque in the ABI).
+struct tn_plan {
+    int device;
+    uint64_t m;
+    uint32_t n;
+    uint64_t windows, levels, ops, aux, temps, big_windows;
+    int64_t t_first, t_last;
+    uint32_t slab_words; // words of every row owned by one CTA when applied (0 = default)
+    uint2 *d_ops;        // [ops]        level-ordered row operations
+    uint32_t *d_lvl;     // [levels + 1] op offset of every level
+    uint32_t *d_aux;     // [aux]        source lists of PULL ops
+    int64_t *d_tbounds;  // [2]          t_first, t_last
+    int32_t *d_status;   // [1]          first asynchronous error
+};
+
+namespace tn {
+// Launch the column-slab streaming kernel for a list of (plan, matrix) jobs.
+tn_status apply_jobs(const tn_plan *const *plans, uint64_t *const *S, const uint32_t *ncols,
+                     const uint32_t *const *src, int64_t *const *t_last, uint32_t count, uint32_t flags,
+                     cudaStream_t stream);
+}  // namespace tn

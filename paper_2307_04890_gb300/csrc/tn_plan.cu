@@ -1,0 +1,708 @@
+// Scheduling of an event batch for the column-slab streaming kernel.
+//
+// Algorithm 1 (Section 3.1) is a strict sequence of row updates, but two
+// events that share no node commute, and the columns of the matrix are
+// independent.  The schedule groups the updates into "levels": inside a level
+// no two updates conflict, so the streaming kernel can issue all of a level's
+// row loads at once and only needs a barrier between levels.
+//
+// Equal timestamps (Section 2.1: adjacency needs dt > 0) are applied as one
+// snapshot.  Inside a group G with node counts c(x) (occurrences of x in G):
+//   * an event whose two ends both occur once in G is an ordinary update
+//     (EVENT: r = S[u] | S[v] into both rows);
+//   * a node y occurring once, whose partner x occurs several times, gets
+//     ONEWAY: S[y] |= S[x] at level L (x is not written at level L);
+//   * a node x occurring several times gets one PULL at level L+1:
+//     S[x] |= OR of its partners' rows, where a partner y occurring once is
+//     read from S[y] (already y_old | x_old: the extra x_old is harmless) and a
+//     partner z occurring several times is read from a saved copy of z's old
+//     row (COPY at level L into a temporary slot).
+// This reproduces S_new[x] = S_old[x] | OR_{(x,y) in G} S_old[y] exactly.
+//
+// The batch is cut into windows of about `window_events` events, never inside
+// a timestamp group.  Each window is scheduled independently by one CTA
+// (levels restart at every window, which acts as one extra barrier):
+//   1. node ids of the window are compacted through a hash table;
+//   2. one thread scans the window's groups in time order and assigns levels
+//      (level of an update = 1 + last level at which any of its rows was
+//      touched), tie-group roles, PULL source lists and COPY slots;
+//   3. the window's updates are counting-sorted by level.
+// A final pass concatenates the windows into one level-ordered op list.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "tn_internal.cuh"
+
+namespace tn {
+
+constexpr int kPlanThreads = 256;
+constexpr uint32_t kDefaultWindow = 2048;
+constexpr uint32_t kEmpty = 0xFFFFFFFFu;
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+
+// event flags stored in the grp array once scheduling is done
+constexpr uint32_t kFlagNoop = 1u << 28;
+constexpr uint32_t kFlagIso = 1u << 29;
+constexpr uint32_t kFlagShA = 1u << 30;
+constexpr uint32_t kFlagShB = 1u << 31;
+
+// arena layout (uint32 words) for a window of E events:
+//   lu[E] lv[E] grp[E] evl[E] run_node[E] run_aux[E] run_lev[E] run_temp[E] scratch[3*Hs]
+// scratch: hash keys + ids (2*H words, H = hash slots) during id assignment,
+// then node state nlev/ncnt/nrun (3*D words, D <= 2E distinct nodes), then the
+// level histogram (<= 2E + 3 words).
+__host__ __device__ inline uint64_t hash_slots(uint64_t E) { return ((3 * E + 31) / 32) * 32; }
+__host__ __device__ inline uint64_t arena_words(uint64_t E)
+{
+    const uint64_t H = hash_slots(E);
+    uint64_t scratch = 2 * H;
+    if (6 * E > scratch) scratch = 6 * E;
+    if (2 * E + 3 > scratch) scratch = 2 * E + 3;
+    return 8 * E + scratch;
+}
+
+struct PlanArgs {
+    const uint32_t *u, *v;
+    const int64_t *t;
+    uint64_t m;
+    uint32_t n;
+    const int64_t *t_after;
+    uint32_t window;     // target events per window
+    uint32_t nw;         // number of windows
+    uint64_t *wstart;    // [nw + 1]
+    uint32_t smem_max_events;
+    // per-window results: nops, nlev, naux, ntemp
+    uint32_t *wcount;    // [4 * nw]
+    // staging (window w uses the regions starting at 3*s_w / 2*s_w + w)
+    uint2 *ops_stage;    // [3m]
+    uint32_t *aux_stage; // [3m]
+    uint32_t *lvl_stage; // [2m + nw + 1]
+    // large windows
+    uint32_t *big_list;  // [nw]
+    uint64_t *big_off;   // [nw]
+    uint32_t *big_arena;
+    // global counters: [0] error flags, [1] number of big windows, [2] arena words of
+    // the big windows, [3] largest window scheduled in shared memory
+    unsigned long long *counters;
+};
+
+// ---------------------------------------------------------------------------
+// validation (Section 2.1: nodes in [0, n), events time-ordered)
+// ---------------------------------------------------------------------------
+__global__ void validate_kernel(PlanArgs a)
+{
+    uint32_t bad = 0;
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < a.m;
+         e += (uint64_t)gridDim.x * blockDim.x) {
+        if (a.u[e] >= a.n || a.v[e] >= a.n) bad |= 1u;
+        if (e > 0 && a.t[e] < a.t[e - 1]) bad |= 2u;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && a.t_after && a.m > 0 && !(a.t[0] > *a.t_after)) bad |= 2u;
+    if (bad) atomicOr(&a.counters[0], (unsigned long long)bad);
+}
+
+// window w starts at the first timestamp-group start at or after w * window
+__global__ void window_kernel(PlanArgs a)
+{
+    for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w <= a.nw;
+         w += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t s;
+        if (w == 0) {
+            s = 0;
+        } else if (w == a.nw) {
+            s = a.m;
+        } else {
+            s = w * (uint64_t)a.window;
+            if (s >= a.m) {
+                s = a.m;
+            } else if (a.t[s] == a.t[s - 1]) {
+                // first index with t > t[s] (upper bound) by binary search
+                const int64_t key = a.t[s];
+                uint64_t lo = s, hi = a.m;
+                while (lo < hi) {
+                    uint64_t mid = lo + (hi - lo) / 2;
+                    if (a.t[mid] > key) hi = mid;
+                    else lo = mid + 1;
+                }
+                s = lo;
+            }
+        }
+        a.wstart[w] = s;
+    }
+}
+
+__global__ void big_window_kernel(PlanArgs a)
+{
+    for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < a.nw;
+         w += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t E = a.wstart[w + 1] - a.wstart[w];
+        if (E <= a.smem_max_events) atomicMax(&a.counters[3], (unsigned long long)E);
+        if (E > a.smem_max_events) {
+            unsigned long long slot = atomicAdd(&a.counters[1], 1ull);
+            unsigned long long off = atomicAdd(&a.counters[2], (unsigned long long)arena_words(E));
+            a.big_list[slot] = (uint32_t)w;
+            a.big_off[slot] = off;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// per-window scheduler
+// ---------------------------------------------------------------------------
+__device__ inline uint32_t hslot(uint32_t key, uint32_t H)
+{
+    return (uint32_t)(((uint64_t)(key * 0x9E3779B1u) * H) >> 32);
+}
+
+__device__ inline void hinsert(uint32_t *hkey, uint32_t H, uint32_t key)
+{
+    uint32_t s = hslot(key, H);
+    for (uint32_t probe = 0; probe < H; ++probe) {  // the table always has free slots
+        uint32_t cur = hkey[s];
+        if (cur == key) return;
+        if (cur == kEmpty) {
+            uint32_t prev = atomicCAS(&hkey[s], kEmpty, key);
+            if (prev == kEmpty || prev == key) return;
+        }
+        s = (s + 1 == H) ? 0 : s + 1;
+    }
+}
+
+__device__ inline uint32_t hlookup(const uint32_t *hkey, const uint32_t *hval, uint32_t H, uint32_t key)
+{
+    uint32_t s = hslot(key, H);
+    for (uint32_t probe = 0; probe < H && hkey[s] != key; ++probe) s = (s + 1 == H) ? 0 : s + 1;
+    return hval[s];
+}
+
+__device__ void schedule_window(const PlanArgs &a, uint32_t w, uint32_t *arena)
+{
+    __shared__ uint32_t warp_sums[32];
+    __shared__ uint32_t tot;
+    __shared__ uint32_t res[5];  // nops, nlev(maxlev), naux, ntemp, nruns
+
+    const uint64_t s = a.wstart[w];
+    const uint32_t E = (uint32_t)(a.wstart[w + 1] - s);
+    uint32_t *cnt = a.wcount + 4ull * w;
+    if (E == 0) {
+        if (threadIdx.x == 0) {
+            cnt[0] = cnt[1] = cnt[2] = cnt[3] = 0;
+            a.lvl_stage[2 * s + w] = 0;
+        }
+        return;
+    }
+    const uint32_t T = blockDim.x, tid = threadIdx.x;
+    const uint32_t H = (uint32_t)hash_slots(E);
+    uint32_t *lu = arena, *lv = lu + E, *grp = lv + E, *evl = grp + E;
+    uint32_t *run_node = evl + E, *run_aux = run_node + E, *run_lev = run_aux + E, *run_temp = run_lev + E;
+    uint32_t *scratch = run_temp + E;
+    uint32_t *hkey = scratch, *hval = scratch + H;
+    const uint32_t *U = a.u + s, *V = a.v + s;
+    const int64_t *Tt = a.t + s;
+
+    // 1. compact node ids
+    for (uint32_t i = tid; i < H; i += T) hkey[i] = kEmpty;
+    __syncthreads();
+    for (uint32_t i = tid; i < E; i += T) {
+        hinsert(hkey, H, U[i]);
+        hinsert(hkey, H, V[i]);
+    }
+    __syncthreads();
+    for (uint32_t i = tid; i < H; i += T) hval[i] = hkey[i] != kEmpty ? 1u : 0u;
+    __syncthreads();
+    const uint32_t D = block_excl_scan_array(hval, H, warp_sums, &tot);
+    for (uint32_t i = tid; i < E; i += T) {
+        lu[i] = hlookup(hkey, hval, H, U[i]);
+        lv[i] = hlookup(hkey, hval, H, V[i]);
+        grp[i] = (i == 0 || Tt[i] != Tt[i - 1]) ? 1u : 0u;
+    }
+    __syncthreads();
+    block_excl_scan_array(grp, E, warp_sums, &tot);  // grp[i] = starts before i
+    for (uint32_t i = tid; i < E; i += T) grp[i] += (i == 0 || Tt[i] != Tt[i - 1]) ? 1u : 0u;
+    // grp[i] is now 1 + group index, which is all the scan below needs.
+    uint32_t *nlev = scratch, *ncnt = scratch + D, *nrun = scratch + 2 * D;
+    __syncthreads();
+    for (uint32_t i = tid; i < D; i += T) {
+        nlev[i] = 0;
+        ncnt[i] = 0;
+        nrun[i] = kNone;
+    }
+    __syncthreads();
+
+    // 2. sequential level scan (one thread), in time order
+    if (tid == 0) {
+        uint32_t nruns = 0, naux = 0, ntemp = 0, maxlev = 0;
+        uint32_t *auxw = a.aux_stage + 3 * s;
+        uint32_t i = 0;
+        while (i < E) {
+            const uint32_t g = grp[i];
+            uint32_t g1 = i + 1;
+            while (g1 < E && grp[g1] == g) ++g1;
+            if (g1 == i + 1) {
+                const uint32_t x = lu[i], y = lv[i];
+                if (x == y) {
+                    grp[i] = kFlagNoop;
+                } else {
+                    const uint32_t L = 1 + max(nlev[x], nlev[y]);
+                    nlev[x] = L;
+                    nlev[y] = L;
+                    evl[i] = L;
+                    grp[i] = kFlagIso;
+                    maxlev = max(maxlev, L);
+                }
+            } else {
+                // occurrences of every node inside the group
+                for (uint32_t j = i; j < g1; ++j) {
+                    ncnt[lu[j]] = 0;
+                    ncnt[lv[j]] = 0;
+                    nrun[lu[j]] = kNone;
+                    nrun[lv[j]] = kNone;
+                }
+                for (uint32_t j = i; j < g1; ++j) {
+                    if (lu[j] == lv[j]) continue;
+                    ++ncnt[lu[j]];
+                    ++ncnt[lv[j]];
+                }
+                const uint32_t run0 = nruns;
+                uint32_t Lc = 0;
+                bool any = false;
+                for (uint32_t j = i; j < g1; ++j) {
+                    const uint32_t x = lu[j], y = lv[j];
+                    if (x == y) {
+                        grp[j] = kFlagNoop;
+                        continue;
+                    }
+                    const bool sx = ncnt[x] > 1, sy = ncnt[y] > 1;
+                    if (!sx && !sy) {
+                        const uint32_t L = 1 + max(nlev[x], nlev[y]);
+                        nlev[x] = L;
+                        nlev[y] = L;
+                        evl[j] = L;
+                        grp[j] = kFlagIso;
+                        maxlev = max(maxlev, L);
+                        continue;
+                    }
+                    any = true;
+                    Lc = max(Lc, max(nlev[x], nlev[y]));
+                    grp[j] = (sx ? kFlagShA : 0u) | (sy ? kFlagShB : 0u);
+                    uint32_t rx = kNone, ry = kNone;
+                    if (sx) {
+                        rx = nrun[x];
+                        if (rx == kNone) {
+                            rx = nruns++;
+                            nrun[x] = rx;
+                            run_node[rx] = U[j];
+                            run_aux[rx] = naux;
+                            run_lev[rx] = 0;  // fill counter until the level is known
+                            run_temp[rx] = kNone;
+                            auxw[naux] = ncnt[x];
+                            naux += 1 + ncnt[x];
+                        }
+                    }
+                    if (sy) {
+                        ry = nrun[y];
+                        if (ry == kNone) {
+                            ry = nruns++;
+                            nrun[y] = ry;
+                            run_node[ry] = V[j];
+                            run_aux[ry] = naux;
+                            run_lev[ry] = 0;
+                            run_temp[ry] = kNone;
+                            auxw[naux] = ncnt[y];
+                            naux += 1 + ncnt[y];
+                        }
+                    }
+                    if (sx && sy) {
+                        if (run_temp[rx] == kNone) run_temp[rx] = ntemp++;
+                        if (run_temp[ry] == kNone) run_temp[ry] = ntemp++;
+                        auxw[run_aux[rx] + 1 + run_lev[rx]++] = kTempRef | run_temp[ry];
+                        auxw[run_aux[ry] + 1 + run_lev[ry]++] = kTempRef | run_temp[rx];
+                    } else if (sx) {
+                        auxw[run_aux[rx] + 1 + run_lev[rx]++] = V[j];
+                    } else {
+                        auxw[run_aux[ry] + 1 + run_lev[ry]++] = U[j];
+                    }
+                }
+                if (any) {
+                    const uint32_t L = Lc + 1;
+                    for (uint32_t j = i; j < g1; ++j) {
+                        const uint32_t f = grp[j];
+                        if (f & (kFlagNoop | kFlagIso)) continue;
+                        evl[j] = L;
+                        nlev[lu[j]] = L + 1;
+                        nlev[lv[j]] = L + 1;
+                    }
+                    for (uint32_t r = run0; r < nruns; ++r) run_lev[r] = L;
+                    maxlev = max(maxlev, L + 1);
+                }
+            }
+            i = g1;
+        }
+        res[0] = 0;
+        res[1] = maxlev;
+        res[2] = naux;
+        res[3] = ntemp;
+        res[4] = nruns;
+    }
+    __syncthreads();
+    const uint32_t maxlev = res[1], nruns = res[4];
+
+    // 3. counting sort of the updates by level (levels 1..maxlev -> 0..maxlev-1)
+    uint32_t *lh = scratch;  // node state is dead
+    for (uint32_t j = tid; j < maxlev + 1; j += T) lh[j] = 0;
+    __syncthreads();
+    for (uint32_t i = tid; i < E; i += T) {
+        const uint32_t f = grp[i];
+        if (f & kFlagNoop) continue;
+        if (f & kFlagIso) {
+            atomicAdd(&lh[evl[i] - 1], 1u);
+        } else {
+            if (!(f & kFlagShA)) atomicAdd(&lh[evl[i] - 1], 1u);
+            if (!(f & kFlagShB)) atomicAdd(&lh[evl[i] - 1], 1u);
+        }
+    }
+    for (uint32_t r = tid; r < nruns; r += T) {
+        atomicAdd(&lh[run_lev[r]], 1u);  // PULL at level L+1 -> index L
+        if (run_temp[r] != kNone) atomicAdd(&lh[run_lev[r] - 1], 1u);
+    }
+    __syncthreads();
+    const uint32_t nops = block_excl_scan_array(lh, maxlev + 1, warp_sums, &tot);
+    uint32_t *lvl_out = a.lvl_stage + 2 * s + w;
+    for (uint32_t j = tid; j < maxlev + 1; j += T) lvl_out[j] = lh[j];
+    __syncthreads();
+    uint2 *ops = a.ops_stage + 3 * s;
+    for (uint32_t i = tid; i < E; i += T) {
+        const uint32_t f = grp[i];
+        if (f & kFlagNoop) continue;
+        const uint32_t x = U[i], y = V[i];
+        const uint32_t L = evl[i] - 1;
+        if (f & kFlagIso) {
+            ops[atomicAdd(&lh[L], 1u)] = make_uint2(op_a(kEvent, x), y);
+        } else {
+            if (!(f & kFlagShA)) ops[atomicAdd(&lh[L], 1u)] = make_uint2(op_a(kOneway, x), y);
+            if (!(f & kFlagShB)) ops[atomicAdd(&lh[L], 1u)] = make_uint2(op_a(kOneway, y), x);
+        }
+    }
+    for (uint32_t r = tid; r < nruns; r += T) {
+        const uint32_t L = run_lev[r];
+        ops[atomicAdd(&lh[L], 1u)] = make_uint2(op_a(kPull, run_node[r]), (uint32_t)(3 * s) + run_aux[r]);
+        if (run_temp[r] != kNone)
+            ops[atomicAdd(&lh[L - 1], 1u)] = make_uint2(op_a(kCopy, run_temp[r]), run_node[r]);
+    }
+    if (tid == 0) {
+        cnt[0] = nops;
+        cnt[1] = maxlev;
+        cnt[2] = res[2];
+        cnt[3] = res[3];
+    }
+}
+
+__global__ void __launch_bounds__(kPlanThreads) schedule_smem_kernel(PlanArgs a)
+{
+    extern __shared__ uint32_t smem_arena[];
+    const uint32_t w = blockIdx.x;
+    const uint64_t E = a.wstart[w + 1] - a.wstart[w];
+    if (E > a.smem_max_events) return;  // scheduled by the large-window kernel
+    schedule_window(a, w, smem_arena);
+}
+
+__global__ void __launch_bounds__(kPlanThreads) schedule_big_kernel(PlanArgs a)
+{
+    const uint32_t w = a.big_list[blockIdx.x];
+    schedule_window(a, w, a.big_arena + a.big_off[blockIdx.x]);
+}
+
+// ---------------------------------------------------------------------------
+// concatenation of the windows
+// ---------------------------------------------------------------------------
+struct Totals {
+    unsigned long long nops, nlev, naux, tmax;
+};
+
+// exclusive scans of nops / nlev / naux over windows (one CTA)
+__global__ void window_scan_kernel(uint32_t *wcount, uint32_t nw, uint64_t *base /* [3*nw] */, Totals *tot)
+{
+    __shared__ uint32_t warp_sums[32];
+    __shared__ uint32_t total;
+    __shared__ unsigned long long carry[3];
+    __shared__ unsigned int tmax;
+    if (threadIdx.x < 3) carry[threadIdx.x] = 0;
+    if (threadIdx.x == 0) tmax = 0;
+    __syncthreads();
+    for (uint32_t c0 = 0; c0 < nw; c0 += blockDim.x) {
+        const uint32_t w = c0 + threadIdx.x;
+        for (int k = 0; k < 3; ++k) {
+            uint32_t x = w < nw ? wcount[4 * w + k] : 0u;
+            uint32_t ex = block_excl_scan_value(x, warp_sums, &total);
+            if (w < nw) base[3ull * w + k] = carry[k] + ex;
+            __syncthreads();
+            if (threadIdx.x == 0) carry[k] += total;
+            __syncthreads();
+        }
+        if (w < nw) atomicMax(&tmax, wcount[4 * w + 3]);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        tot->nops = carry[0];
+        tot->nlev = carry[1];
+        tot->naux = carry[2];
+        tot->tmax = tmax;
+    }
+}
+
+__global__ void compact_kernel(const uint64_t *wstart, const uint32_t *wcount, const uint64_t *base, uint32_t nw,
+                               const uint2 *ops_stage, const uint32_t *aux_stage, const uint32_t *lvl_stage,
+                               uint2 *ops, uint32_t *aux, uint32_t *lvl, uint64_t total_ops, uint64_t total_lev)
+{
+    const uint32_t w = blockIdx.x;
+    if (w >= nw) return;
+    const uint64_t s = wstart[w];
+    const uint32_t nops = wcount[4 * w], nlev = wcount[4 * w + 1], naux = wcount[4 * w + 2];
+    const uint64_t ob = base[3ull * w], lb = base[3ull * w + 1], ab = base[3ull * w + 2];
+    const uint2 *os = ops_stage + 3 * s;
+    for (uint32_t k = threadIdx.x; k < nops; k += blockDim.x) {
+        uint2 op = os[k];
+        if ((op.x >> kKindShift) == kPull) op.y = (uint32_t)(op.y - 3 * s + ab);
+        ops[ob + k] = op;
+    }
+    const uint32_t *as = aux_stage + 3 * s;
+    for (uint32_t k = threadIdx.x; k < naux; k += blockDim.x) aux[ab + k] = as[k];
+    const uint32_t *ls = lvl_stage + 2 * s + w;
+    for (uint32_t j = threadIdx.x; j < nlev; j += blockDim.x) lvl[lb + j] = (uint32_t)(ob + ls[j]);
+    if (w == 0 && threadIdx.x == 0) lvl[total_lev] = (uint32_t)total_ops;
+}
+
+__global__ void tbounds_kernel(const int64_t *t, uint64_t m, int64_t *out)
+{
+    out[0] = t[0];
+    out[1] = t[m - 1];
+}
+
+// shared-memory budget of the per-window scheduler
+static uint32_t smem_max_events()
+{
+    static uint32_t cached = 0;
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
+    if (cached) return cached;
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    uint64_t budget = (uint64_t)optin - 1024;  // static shared memory of the kernel
+    uint32_t E = 64;
+    while (arena_words(E + 64) * 4 <= budget) E += 64;
+    cached = E;
+    return cached;
+}
+
+template <typename T>
+static cudaError_t alloc_async(T **p, uint64_t count, cudaStream_t st)
+{
+    *p = nullptr;
+    if (count == 0) return cudaSuccess;
+    return cudaMallocAsync((void **)p, count * sizeof(T), st);
+}
+
+}  // namespace tn
+
+using namespace tn;
+
+extern "C" tn_status tn_plan_create(const uint32_t *u, const uint32_t *v, const int64_t *t, uint64_t m,
+                                    uint32_t n, const int64_t *t_after, const tn_plan_options *opt,
+                                    void *stream, tn_plan **plan_out)
+{
+    if (!plan_out) return TN_EINVAL;
+    *plan_out = nullptr;
+    if (!u || !v || !t || m == 0 || n == 0 || n >= (1u << 30) || m >= (1ull << 30)) return TN_EINVAL;
+    if (opt) {
+        for (int i = 0; i < 6; ++i)
+            if (opt->reserved[i]) return TN_EINVAL;
+        const uint32_t sw = opt->slab_words;
+        if (sw != 0 && sw != 2 && sw != 4 && sw != 8 && sw != 16) return TN_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    tn_internal_keep_pool();
+    uint32_t window = (opt && opt->window_events) ? opt->window_events : kDefaultWindow;
+    if (window < 32) window = 32;
+
+    PlanArgs a;
+    memset(&a, 0, sizeof(a));
+    a.u = u;
+    a.v = v;
+    a.t = t;
+    a.m = m;
+    a.n = n;
+    a.t_after = t_after;
+    a.window = window;
+    a.nw = (uint32_t)((m + window - 1) / window);
+    a.smem_max_events = smem_max_events();
+
+    tn_plan *p = (tn_plan *)calloc(1, sizeof(tn_plan));
+    if (!p) return TN_ENOMEM;
+    cudaGetDevice(&p->device);
+    p->m = m;
+    p->n = n;
+    p->windows = a.nw;
+    p->slab_words = opt ? opt->slab_words : 0;
+
+    tn_status rc = TN_OK;
+    unsigned long long host_counters[4] = {0, 0, 0, 0};
+    Totals host_tot = {0, 0, 0, 0};
+    uint64_t *base = nullptr;
+    Totals *d_tot = nullptr;
+    const int vblocks = (int)((m + 255) / 256 < 4096 ? (m + 255) / 256 : 4096);
+    const int wblocks = (int)((a.nw + 256) / 256);
+    cudaError_t err = cudaSuccess;
+
+#define TN_STEP(expr)                  \
+    do {                               \
+        err = (expr);                  \
+        if (err != cudaSuccess) goto fail; \
+    } while (0)
+
+    TN_STEP(alloc_async(&a.counters, 4, st));
+    TN_STEP(alloc_async(&a.wstart, (uint64_t)a.nw + 1, st));
+    TN_STEP(alloc_async(&a.wcount, 4ull * a.nw, st));
+    TN_STEP(alloc_async(&a.big_list, (uint64_t)a.nw, st));
+    TN_STEP(alloc_async(&a.big_off, (uint64_t)a.nw, st));
+    TN_STEP(cudaMemsetAsync(a.counters, 0, 4 * sizeof(unsigned long long), st));
+    tn_internal_count_launches(1);
+    validate_kernel<<<vblocks, 256, 0, st>>>(a);
+    tn_internal_count_launches(1);
+    window_kernel<<<wblocks, 256, 0, st>>>(a);
+    tn_internal_count_launches(1);
+    big_window_kernel<<<wblocks, 256, 0, st>>>(a);
+    TN_STEP(cudaGetLastError());
+    TN_STEP(cudaMemcpyAsync(host_counters, a.counters, sizeof(host_counters), cudaMemcpyDeviceToHost, st));
+    TN_STEP(cudaStreamSynchronize(st));
+    if (host_counters[0] & 1ull) {
+        rc = TN_ERANGE;
+        goto done;
+    }
+    if (host_counters[0] & 2ull) {
+        rc = TN_EORDER;
+        goto done;
+    }
+    p->big_windows = host_counters[1];
+
+    TN_STEP(alloc_async(&a.ops_stage, 3 * m, st));
+    TN_STEP(alloc_async(&a.aux_stage, 3 * m, st));
+    TN_STEP(alloc_async(&a.lvl_stage, 2 * m + a.nw + 1, st));
+    TN_STEP(alloc_async(&a.big_arena, host_counters[2], st));
+    {
+        const size_t smem = arena_words(host_counters[3] ? host_counters[3] : 1) * 4;
+        TN_STEP(cudaFuncSetAttribute(schedule_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        tn_internal_count_launches(1);
+        schedule_smem_kernel<<<a.nw, kPlanThreads, smem, st>>>(a);
+        if (host_counters[1]) {
+            tn_internal_count_launches(1);
+            schedule_big_kernel<<<(unsigned)host_counters[1], kPlanThreads, 0, st>>>(a);
+        }
+        TN_STEP(cudaGetLastError());
+    }
+    TN_STEP(alloc_async(&base, 3ull * a.nw, st));
+    TN_STEP(alloc_async(&d_tot, 1, st));
+    tn_internal_count_launches(1);
+    window_scan_kernel<<<1, 1024, 0, st>>>(a.wcount, a.nw, base, d_tot);
+    TN_STEP(cudaGetLastError());
+    TN_STEP(cudaMemcpyAsync(&host_tot, d_tot, sizeof(Totals), cudaMemcpyDeviceToHost, st));
+    TN_STEP(cudaStreamSynchronize(st));
+
+    p->levels = host_tot.nlev;
+    p->ops = host_tot.nops;
+    p->aux = host_tot.naux;
+    p->temps = host_tot.tmax;
+    TN_STEP(alloc_async(&p->d_ops, p->ops + 2, st));  // bulk copies may read one op past a level
+    TN_STEP(alloc_async(&p->d_lvl, p->levels + 1, st));
+    TN_STEP(alloc_async(&p->d_aux, p->aux > 0 ? p->aux : 1, st));
+    TN_STEP(alloc_async(&p->d_tbounds, 2, st));
+    TN_STEP(alloc_async(&p->d_status, 1, st));
+    TN_STEP(cudaMemsetAsync(p->d_status, 0, sizeof(int32_t), st));
+    tn_internal_count_launches(1);
+    compact_kernel<<<a.nw, 256, 0, st>>>(a.wstart, a.wcount, base, a.nw, a.ops_stage, a.aux_stage, a.lvl_stage,
+                                         p->d_ops, p->d_aux, p->d_lvl, p->ops, p->levels);
+    tn_internal_count_launches(1);
+    tbounds_kernel<<<1, 1, 0, st>>>(t, m, p->d_tbounds);
+    TN_STEP(cudaGetLastError());
+    {
+        int64_t tb[2];
+        TN_STEP(cudaMemcpyAsync(tb, t, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        TN_STEP(cudaMemcpyAsync(tb + 1, t + (m - 1), sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        TN_STEP(cudaStreamSynchronize(st));
+        p->t_first = tb[0];
+        p->t_last = tb[1];
+    }
+    goto done;
+
+fail:
+    tn_internal_set_cuda_error(err);
+    rc = err == cudaErrorMemoryAllocation ? TN_ENOMEM : TN_ECUDA;
+done:
+    cudaFreeAsync(a.counters, st);
+    cudaFreeAsync(a.wstart, st);
+    cudaFreeAsync(a.wcount, st);
+    cudaFreeAsync(a.big_list, st);
+    cudaFreeAsync(a.big_off, st);
+    if (a.ops_stage) cudaFreeAsync(a.ops_stage, st);
+    if (a.aux_stage) cudaFreeAsync(a.aux_stage, st);
+    if (a.lvl_stage) cudaFreeAsync(a.lvl_stage, st);
+    if (a.big_arena) cudaFreeAsync(a.big_arena, st);
+    if (base) cudaFreeAsync(base, st);
+    if (d_tot) cudaFreeAsync(d_tot, st);
+    if (rc != TN_OK) {
+        if (p->d_ops) cudaFreeAsync(p->d_ops, st);
+        if (p->d_lvl) cudaFreeAsync(p->d_lvl, st);
+        if (p->d_aux) cudaFreeAsync(p->d_aux, st);
+        if (p->d_tbounds) cudaFreeAsync(p->d_tbounds, st);
+        if (p->d_status) cudaFreeAsync(p->d_status, st);
+        free(p);
+        return rc;
+    }
+    *plan_out = p;
+    return TN_OK;
+#undef TN_STEP
+}
+
+extern "C" tn_status tn_plan_destroy(tn_plan *p, void *stream)
+{
+    if (!p) return TN_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaFreeAsync(p->d_ops, st);
+    cudaFreeAsync(p->d_lvl, st);
+    cudaFreeAsync(p->d_aux, st);
+    cudaFreeAsync(p->d_tbounds, st);
+    cudaFreeAsync(p->d_status, st);
+    free(p);
+    return TN_OK;
+}
+
+extern "C" tn_status tn_plan_get_stats(const tn_plan *p, tn_plan_stats *s)
+{
+    if (!p || !s) return TN_EINVAL;
+    memset(s, 0, sizeof(*s));
+    s->events = p->m;
+    s->windows = p->windows;
+    s->levels = p->levels;
+    s->ops = p->ops;
+    s->aux = p->aux;
+    s->temps = p->temps;
+    s->big_windows = p->big_windows;
+    s->t_first = p->t_first;
+    s->t_last = p->t_last;
+    return TN_OK;
+}
+
+extern "C" tn_status tn_plan_status(tn_plan *p, void *stream)
+{
+    if (!p) return TN_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    int32_t h = 0;
+    TN_CUDA_TRY(cudaMemcpyAsync(&h, p->d_status, sizeof(h), cudaMemcpyDeviceToHost, st));
+    TN_CUDA_TRY(cudaMemsetAsync(p->d_status, 0, sizeof(int32_t), st));
+    TN_CUDA_TRY(cudaStreamSynchronize(st));
+    return (tn_status)h;
+}

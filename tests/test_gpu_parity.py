@@ -1,0 +1,314 @@
+"""Parity of the CUDA path with the CPU oracle (needs a GPU: -m gpu).
+
+Integer work throughout, so every comparison is bit-exact: the full component
+matrix (including zero padding), out- and in-sizes, argmax, hash tables,
+super-events and fused estimates.  Large configurations are checked on seeded
+column samples that the oracle computes exactly (columns are independent).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from conftest import golden_names, load_golden
+from paper_2307_04890_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    import paper_2307_04890_gb300 as tn
+    from paper_2307_04890_gb300.build import build_library
+
+    build_library()
+    oracle.build_oracle()
+
+
+def dev_events(u, v, t):
+    d = torch.device("cuda")
+    return (torch.from_numpy(np.ascontiguousarray(u, np.uint32).view(np.int32)).to(d),
+            torch.from_numpy(np.ascontiguousarray(v, np.uint32).view(np.int32)).to(d),
+            torch.from_numpy(np.ascontiguousarray(t, np.int64)).to(d))
+
+
+def host_matrix(S, ncols):
+    """GPU matrix -> uint64 [rows, ceil(ncols/64)], asserting zero padding."""
+    a = S.cpu().numpy().view(np.uint64)
+    w = (ncols + 63) // 64
+    assert not a[:, w:].any(), "padding words must stay zero"
+    if ncols % 64:
+        assert not (a[:, w - 1] >> np.uint64(ncols % 64)).any(), "padding bits must stay zero"
+    return a[:, :w]
+
+
+def gpu_matrix(u, v, t, n, **kw):
+    du, dv, dt = dev_events(u, v, t)
+    S = tn.tn_component_matrix(du, dv, dt, n, **kw)
+    torch.cuda.synchronize()
+    return host_matrix(S, n)
+
+
+def u32(x):
+    return x.cpu().numpy().view(np.uint32)
+
+
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("name", golden_names())
+def test_golden(name):
+    n, events, oc, rows = load_golden(name)
+    ev = np.array(events, np.int64).reshape(-1, 3)
+    u, v, t = ev[:, 0].astype(np.uint32), ev[:, 1].astype(np.uint32), ev[:, 2]
+    B = oracle.to_bool(gpu_matrix(u, v, t, n), n)
+    for j, want in oc.items():
+        assert sorted(np.flatnonzero(B[:, j]).tolist()) == want
+    for i, want in rows.items():
+        assert sorted(np.flatnonzero(B[i]).tolist()) == want
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_fuzz_dense_ties(seed):
+    rng = np.random.default_rng(500 + seed)
+    n = int(rng.integers(1, 71))
+    m = int(rng.integers(1, 301))
+    u = rng.integers(0, n, m).astype(np.uint32)
+    v = rng.integers(0, n, m).astype(np.uint32)
+    t = np.sort(rng.integers(0, int(rng.integers(1, 12)), m))
+    win = int(rng.choice([32, 64, 2048]))
+    du, dv, dt = dev_events(u, v, t)
+    plan = tn.Plan(du, dv, dt, n, window_events=win, slab_words=int(rng.choice([2, 4, 8, 16])))
+    S = torch.empty((n, tn.tn_row_words(n)), dtype=torch.int64, device="cuda")
+    plan.apply(S, init=True)
+    assert plan.status() == 0
+    assert np.array_equal(host_matrix(S, n), oracle.component_matrix(u, v, t, n))
+
+
+def test_config1_full():
+    """n=1000, m=20000, uniform pairs, t uniform in [0, 1e4) (dense ties)."""
+    n = 1000
+    u, v, t = synth.uniform_events(n, 20000, t_range=10**4, seed=1)
+    du, dv, dt = dev_events(u, v, t)
+    S = tn.tn_component_matrix(du, dv, dt, n)
+    out, ins, am = tn.tn_out_sizes(S, n, n, in_sizes=True, argmax=True)
+    torch.cuda.synchronize()
+    ref = oracle.component_matrix(u, v, t, n)
+    assert np.array_equal(host_matrix(S, n), ref)
+    want = oracle.column_counts(ref, n)
+    assert np.array_equal(u32(out), want)
+    assert np.array_equal(u32(ins), oracle.row_counts(ref))
+    assert int(am.item()) == oracle.argmax(want)
+    B = oracle.to_bool(ref, n)
+    for j in np.random.default_rng(0).choice(n, 25, replace=False):  # brute-force SI
+        assert np.array_equal(B[:, j], oracle.si_reach(u, v, t, n, int(j)))
+
+
+@pytest.mark.parametrize("slab", [2, 4, 8, 16])
+@pytest.mark.parametrize("window", [40, 700, 4096])
+def test_schedule_options_identical(slab, window):
+    n = 1500  # several slabs, ragged last slab, several windows, ragged last window
+    u, v, t = synth.uniform_events(n, 31_001, t_range=12_000, seed=3)
+    du, dv, dt = dev_events(u, v, t)
+    plan = tn.Plan(du, dv, dt, n, window_events=window, slab_words=slab)
+    S = torch.empty((n, tn.tn_row_words(n)), dtype=torch.int64, device="cuda")
+    plan.apply(S, init=True)
+    assert plan.status() == 0
+    assert np.array_equal(host_matrix(S, n), oracle.component_matrix(u, v, t, n))
+
+
+def test_activity_driven_medium():
+    n = 3000
+    u, v, t = synth.activity_driven(n, 200_000, seed=4)
+    assert np.array_equal(gpu_matrix(u, v, t, n), oracle.component_matrix(u, v, t, n))
+
+
+def test_bursty_medium_big_groups():
+    """Power-law + Pareto times rounded to seconds: large tie groups with hubs."""
+    n = 20_000
+    u, v, t = synth.powerlaw_bursty(n, 150_000, seed=5)
+    ref = oracle.component_matrix(u, v, t, n, src=np.arange(0, n, 37, dtype=np.uint32))
+    du, dv, dt = dev_events(u, v, t)
+    src = torch.arange(0, n, 37, dtype=torch.int32, device="cuda")
+    S = tn.tn_component_columns(du, dv, dt, n, src)
+    torch.cuda.synchronize()
+    assert np.array_equal(host_matrix(S, src.numel()), ref)
+
+
+def test_single_giant_group():
+    """All events share one timestamp: the window exceeds the shared-memory
+    scheduler and takes the large-window path; S = I + adjacency."""
+    n, m = 3000, 20_000
+    rng = np.random.default_rng(6)
+    u = rng.integers(0, n, m).astype(np.uint32)
+    v = rng.integers(0, n, m).astype(np.uint32)
+    t = np.full(m, 7, np.int64)
+    du, dv, dt = dev_events(u, v, t)
+    plan = tn.Plan(du, dv, dt, n)
+    assert plan.stats()["big_windows"] >= 1
+    S = torch.empty((n, tn.tn_row_words(n)), dtype=torch.int64, device="cuda")
+    plan.apply(S, init=True)
+    assert plan.status() == 0
+    assert np.array_equal(host_matrix(S, n), oracle.component_matrix(u, v, t, n))
+
+
+def test_mixed_giant_and_small_groups():
+    rng = np.random.default_rng(8)
+    n = 2000
+    parts = []
+    for g in range(30):
+        size = int(rng.choice([1, 2, 5, 9000 if g in (7, 21) else 40]))
+        parts.append((rng.integers(0, n, size), rng.integers(0, n, size), np.full(size, g)))
+    u = np.concatenate([p[0] for p in parts]).astype(np.uint32)
+    v = np.concatenate([p[1] for p in parts]).astype(np.uint32)
+    t = np.concatenate([p[2] for p in parts]).astype(np.int64)
+    assert np.array_equal(gpu_matrix(u, v, t, n), oracle.component_matrix(u, v, t, n))
+
+
+def test_self_loops_only_and_empty():
+    n = 100
+    u = np.arange(50, dtype=np.uint32)
+    assert np.array_equal(gpu_matrix(u, u, np.arange(50), n), oracle.init_sources(n)[:, :2])
+    S = torch.empty((n, tn.tn_row_words(n)), dtype=torch.int64, device="cuda")
+    e = torch.empty(0, dtype=torch.int32, device="cuda")
+    tn.tn_component_matrix(e, e, torch.empty(0, dtype=torch.int64, device="cuda"), n, S=S)
+    torch.cuda.synchronize()
+    assert np.array_equal(host_matrix(S, n), oracle.init_sources(n))
+
+
+def test_incremental_batches_with_t_last():
+    n = 800
+    u, v, t = synth.uniform_events(n, 24_000, t_range=9_000, seed=9)
+    du, dv, dt = dev_events(u, v, t)
+    S = torch.empty((n, tn.tn_row_words(n)), dtype=torch.int64, device="cuda")
+    t_last = torch.full((1,), -(2**62), dtype=torch.int64, device="cuda")
+    first = True
+    for a, b in synth.split_batches(t, 4):
+        tn.tn_component_matrix(du[a:b], dv[a:b], dt[a:b], n, S=S, t_last=t_last, init=first)
+        first = False
+    torch.cuda.synchronize()
+    assert int(t_last.item()) == int(t[-1])
+    assert np.array_equal(host_matrix(S, n), oracle.component_matrix(u, v, t, n))
+    # a batch that does not start after t_last is rejected, S untouched
+    before = S.clone()
+    with pytest.raises(tn.TnError) as e:
+        tn.tn_component_matrix(du[:10], dv[:10], dt[:10], n, S=S, t_last=t_last, init=False)
+    assert e.value.status == tn.TN_EORDER
+    assert torch.equal(before, S)
+
+
+def test_plan_apply_order_gate():
+    n = 50
+    u, v, t = synth.uniform_events(n, 500, t_range=100, seed=10)
+    du, dv, dt = dev_events(u, v, t)
+    plan = tn.Plan(du, dv, dt, n)
+    S = torch.empty((n, tn.tn_row_words(n)), dtype=torch.int64, device="cuda")
+    t_last = torch.full((1,), int(t[-1]), dtype=torch.int64, device="cuda")
+    plan.apply(S, t_last=t_last, init=True)
+    assert plan.status() == tn.TN_EORDER
+    assert plan.status() == 0  # cleared by reading
+
+
+def test_validation_errors():
+    n = 10
+    du, dv, dt = dev_events(np.array([1, 2]), np.array([3, 10]), np.array([0, 1]))
+    with pytest.raises(tn.TnError) as e:
+        tn.tn_component_matrix(du, dv, dt, n)
+    assert e.value.status == tn.TN_ERANGE
+    du, dv, dt = dev_events(np.array([1, 2]), np.array([3, 4]), np.array([5, 1]))
+    with pytest.raises(tn.TnError) as e:
+        tn.tn_component_matrix(du, dv, dt, n)
+    assert e.value.status == tn.TN_EORDER
+
+
+def test_column_subset_repeats():
+    n = 700
+    u, v, t = synth.uniform_events(n, 9000, t_range=3000, seed=12)
+    src = np.array([5, 5, 699, 0, 311] * 30, np.uint32)
+    du, dv, dt = dev_events(u, v, t)
+    S = tn.tn_component_columns(du, dv, dt, n, torch.from_numpy(src.view(np.int32)).cuda())
+    out, _, _ = tn.tn_out_sizes(S, n, len(src))
+    torch.cuda.synchronize()
+    ref = oracle.component_matrix(u, v, t, n, src=src)
+    assert np.array_equal(host_matrix(S, len(src)), ref)
+    assert np.array_equal(u32(out), oracle.column_counts(ref, len(src)))
+
+
+def test_batched_apply_equals_single():
+    plans, mats, refs = [], [], []
+    for i, (n, m) in enumerate([(300, 4000), (1200, 9000), (64, 700), (2500, 30000)]):
+        u, v, t = synth.uniform_events(n, m, t_range=m // 2, seed=20 + i)
+        du, dv, dt = dev_events(u, v, t)
+        plans.append(tn.Plan(du, dv, dt, n, slab_words=[2, 4, 8, 4][i]))
+        mats.append(torch.empty((n, tn.tn_row_words(n)), dtype=torch.int64, device="cuda"))
+        refs.append(oracle.component_matrix(u, v, t, n))
+    tn.tn_plan_apply_batch(plans, mats)
+    torch.cuda.synchronize()
+    for p, S, ref in zip(plans, mats, refs):
+        assert p.status() == 0
+        assert np.array_equal(host_matrix(S, p.n), ref)
+
+
+def test_host_entry_point():
+    n = 900
+    u, v, t = synth.activity_driven(n, 40_000, seed=13)
+    sizes, am = tn.tn_out_component_sizes_host(u, v, t, n)
+    ref = oracle.column_counts(oracle.component_matrix(u, v, t, n), n)
+    assert np.array_equal(sizes, ref)
+    assert am == oracle.argmax(ref)
+
+
+# --------------------------------------------------------------------------
+# hashing (Section 4)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("n,k,R,seed", [(1000, 97, 3, 1), (70_000, 4096, 2, 123456789), (5, 1, 1, 0)])
+def test_hash_tables_and_super_events(n, k, R, seed):
+    u, v, t = synth.uniform_events(n, 5000, t_range=1000, seed=seed % 1000, self_loops=True)
+    du, dv, dt = dev_events(u, v, t)
+    H, pu, pv = tn.tn_hash_proxy(du, dv, n, k, R, seed)
+    torch.cuda.synchronize()
+    Href = oracle.hash_nodes(seed, R, k, n)
+    assert np.array_equal(u32(H), Href)
+    for j in range(R):
+        a, b = oracle.proxy_events(u, v, Href[j])
+        assert np.array_equal(u32(pu[j]), a) and np.array_equal(u32(pv[j]), b)
+
+
+@pytest.mark.parametrize("n,m,k,R", [(400, 3000, 37, 3), (3000, 60_000, 512, 8), (150, 120, 60, 5)])
+def test_estimate_matches_oracle(n, m, k, R):
+    u, v, t = synth.uniform_events(n, m, t_range=m // 3, seed=k)
+    du, dv, dt = dev_events(u, v, t)
+    H, pu, pv = tn.tn_hash_proxy(du, dv, n, k, R, 77)
+    P = torch.empty((R, k, tn.tn_row_words(k)), dtype=torch.int64, device="cuda")
+    plans = [tn.Plan(pu[j].contiguous(), pv[j].contiguous(), dt, k) for j in range(R)]
+    tn.tn_plan_apply_batch(plans, [P[j] for j in range(R)])
+    est = tn.tn_hash_estimate(P, R, k, H, n)
+    src = torch.tensor([0, n - 1, n // 2, 3], dtype=torch.int32, device="cuda")
+    est_sub = tn.tn_hash_estimate(P, R, k, H, n, src=src)
+    torch.cuda.synchronize()
+    Href = oracle.hash_nodes(77, R, k, n)
+    Pref = oracle.proxy_matrices(u, v, t, Href, k)
+    for j in range(R):
+        assert np.array_equal(host_matrix(P[j], k), Pref[j])
+    want = oracle.hash_estimate(Pref, Href, n)
+    assert np.array_equal(u32(est), want)
+    assert np.array_equal(u32(est_sub), want[[0, n - 1, n // 2, 3]])
+    exact = oracle.column_counts(oracle.component_matrix(u, v, t, n), n)
+    assert (want >= exact).all()  # containment (Section 4.2)
+
+
+def test_estimate_global_table_path():
+    """R * k beyond the shared-memory table: the per-CTA table lives in global memory."""
+    n, m, k, R = 2000, 20_000, 40_000, 6
+    u, v, t = synth.uniform_events(n, m, t_range=m, seed=31)
+    du, dv, dt = dev_events(u, v, t)
+    H, pu, pv = tn.tn_hash_proxy(du, dv, n, k, R, 3)
+    P = torch.empty((R, k, tn.tn_row_words(k)), dtype=torch.int64, device="cuda")
+    for j in range(R):
+        tn.tn_component_matrix(pu[j].contiguous(), pv[j].contiguous(), dt, k, S=P[j])
+    src = torch.arange(0, n, 13, dtype=torch.int32, device="cuda")
+    est = tn.tn_hash_estimate(P, R, k, H, n, src=src)
+    torch.cuda.synchronize()
+    Href = oracle.hash_nodes(3, R, k, n)
+    Pref = np.stack([host_matrix(P[j], k) for j in range(R)])
+    ref_src = np.arange(0, n, 13, dtype=np.uint32)
+    # proxies were checked elsewhere; here the fusion over them is compared
+    assert np.array_equal(u32(est), oracle.hash_estimate(Pref, Href, n, ref_src))
+    pu0, pv0 = oracle.proxy_events(u, v, Href[0])
+    assert np.array_equal(Pref[0], oracle.component_matrix(pu0, pv0, t, k))
