@@ -286,7 +286,7 @@ def main():
               "config": {"workload": w["desc"], "n": n, "m": m, "global_batch": m * world,
                          "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                          "l2": "inputs larger than L2 (S %.2f GB, events %.0f MB)" % (n * W * 8 / 1e9, m * 16 / 1e6),
-                         "window_events": args.window or 2048, "slab_words": args.slab or 4,
+                         "window_events": args.window or 640, "slab_words": args.slab or 16,
                          "levels": stats["levels"], "ops": stats["ops"]},
               "events_per_s": world * m / (ms_step * 1e-3),
               "roofline": roofline, "gpu_launches": launches, "clocks": clocks.summary(),

@@ -23,7 +23,7 @@
  * Layout of a component matrix (all entry points)
  *   A matrix with `n_rows` rows and `ncols` source columns is stored row-major
  *   as uint64 words.  Each row occupies tn_row_words(ncols) words (a multiple of
- *   4 words = 32 bytes, so rows are 32-byte aligned); bit c of row i is
+ *   16 words = 128 bytes, so rows are 128-byte aligned); bit c of row i is
  *       (S[i * tn_row_words(ncols) + c / 64] >> (c % 64)) & 1
  *   and means "node i has been reached from source column c".  Bits at column
  *   positions >= ncols are zero on output.  For the full matrix ncols = n and
@@ -84,7 +84,7 @@ const char *tn_status_string(tn_status status);
 const char *tn_last_cuda_error(void);
 
 /* Row stride, in uint64 words, of a matrix with `ncols` source columns:
- * ceil(ncols / 256) * 4 (rows padded to 32 bytes).  tn_row_words(0) = 0. */
+ * ceil(ncols / 1024) * 16 (rows padded to 128 bytes).  tn_row_words(0) = 0. */
 uint64_t tn_row_words(uint64_t ncols);
 
 /* ---------------------------------------------------------------------------
@@ -168,10 +168,14 @@ tn_status tn_out_sizes(const uint64_t *S, uint32_t n_rows, uint32_t ncols,
 typedef struct tn_plan tn_plan;
 
 typedef struct tn_plan_options {
-    uint32_t window_events; /* target events per scheduling window (0 = default 2048) */
+    uint32_t window_events; /* target events per scheduling window (0 = default 640) */
     uint32_t slab_words;    /* 64-bit words of every row owned by one CTA when the
-                               plan is applied: 2, 4, 8 or 16 (0 = default 4) */
-    uint32_t reserved[6];   /* must be zero */
+                               plan is applied: 2, 4, 8 or 16 (0 = default 16) */
+    uint32_t smem_rows;     /* row slots of the streaming kernel's shared-memory row
+                               buffer (at most 160 KB / (8 slab_words)); windows with
+                               more rows (plus saved copies) stream from global
+                               memory (0 = 160 KB / (8 slab_words)) */
+    uint32_t reserved[5];   /* must be zero */
 } tn_plan_options;
 
 typedef struct tn_plan_stats {
@@ -181,7 +185,9 @@ typedef struct tn_plan_stats {
     uint64_t ops;        /* row operations after tie handling */
     uint64_t aux;        /* source-list entries of multi-source updates */
     uint64_t temps;      /* saved-row slots needed by tie groups (max per window) */
-    uint64_t big_windows;/* windows scheduled by the large-window path */
+    uint64_t big_windows;  /* windows scheduled by the large-window path */
+    uint64_t local_windows;/* windows applied in shared memory */
+    uint64_t items;        /* work items of the streaming kernel */
     int64_t t_first, t_last;
 } tn_plan_stats;
 

@@ -50,13 +50,14 @@ class TnError(RuntimeError):
 
 class _Options(ctypes.Structure):
     _fields_ = [("window_events", ctypes.c_uint32), ("slab_words", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 6)]
+                ("smem_rows", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 5)]
 
 
 class _Stats(ctypes.Structure):
     _fields_ = [("events", ctypes.c_uint64), ("windows", ctypes.c_uint64), ("levels", ctypes.c_uint64),
                 ("ops", ctypes.c_uint64), ("aux", ctypes.c_uint64), ("temps", ctypes.c_uint64),
-                ("big_windows", ctypes.c_uint64), ("t_first", ctypes.c_int64), ("t_last", ctypes.c_int64)]
+                ("big_windows", ctypes.c_uint64), ("local_windows", ctypes.c_uint64), ("items", ctypes.c_uint64),
+                ("t_first", ctypes.c_int64), ("t_last", ctypes.c_int64)]
 
 
 def load_library(path: str | None = None):
@@ -269,11 +270,11 @@ class Plan:
     """A validated, scheduled event batch (tn_plan_create / tn_plan_apply)."""
 
     def __init__(self, u, v, t, n: int, t_after=None, window_events: int = 0, slab_words: int = 0,
-                 stream=None):
+                 smem_rows: int = 0, stream=None):
         lib = load_library()
         self.m = _events(u, v, t)
         self.n = n
-        opt = _Options(window_events, slab_words)
+        opt = _Options(window_events, slab_words, smem_rows)
         h = ctypes.c_void_p()
         if t_after is not None:
             _dev(t_after, ("int64",), "t_after")

@@ -47,7 +47,7 @@ extern "C" const char *tn_status_string(tn_status s)
     }
 }
 
-extern "C" uint64_t tn_row_words(uint64_t ncols) { return ((ncols + 255) / 256) * 4; }
+extern "C" uint64_t tn_row_words(uint64_t ncols) { return ((ncols + 1023) / 1024) * 16; }
 
 // Whole exact path from host arrays: H2D copy of the events, component matrix
 // from the identity (Algorithm 1), out-sizes (Section 3.1), D2H copy.

@@ -8,7 +8,7 @@
 //     memory stages with bulk asynchronous copies (cp.async.bulk, completion on
 //     an mbarrier), so the ops are read from L2/HBM once per CTA and without
 //     occupying the consumer threads;
-//   * eight consumer warps apply a tile: for each op, 128-bit loads of the two
+//   * four consumer warps apply a tile: for each op, 128-bit loads of the two
 //     row segments, OR, 128-bit stores (four ops in flight per thread); the
 //     per-tile named barrier orders one level's stores before the next level's
 //     loads.
@@ -24,23 +24,21 @@
 
 namespace tn {
 
-constexpr int kConsumerWarps = 8;
+constexpr int kConsumerWarps = 4;
 constexpr int kConsumers = 32 * kConsumerWarps;
 constexpr int kThreads = kConsumers + 32;
-constexpr int kStages = 4;
-constexpr uint32_t kTileOps = 2048;
-constexpr uint32_t kStageOps = kTileOps + 2;
-constexpr uint32_t kEndTile = 0xFFFFFFFFu;
+constexpr int kStages = 2;
+constexpr uint32_t kEndItem = 0xFFFFFFFFu;
 constexpr int kMaxJobs = 24;
 
 struct Job {
-    const uint2 *ops;
-    const uint32_t *lvl;
+    const uint2 *blob;
+    const uint4 *items;
     const uint32_t *aux;
-    uint64_t nlev;
+    uint64_t nitems;
     uint64_t *S;
     uint64_t ld;    // row stride in words
-    uint64_t *tmp;  // saved-row slots, ld words each
+    uint64_t *tmp;  // saved-row slots of global windows, ld words each
     int32_t *status;
     uint32_t sw;    // slab words per CTA (power of two >= 2)
     uint32_t lsw;   // log2(sw)
@@ -53,9 +51,11 @@ struct JobList {
     uint32_t count;
 };
 
-struct TileHdr {
-    uint32_t count;  // ops in the tile, kEndTile = no more tiles
-    uint32_t off;    // first op's index inside the stage buffer (0 or 1)
+struct StageHdr {
+    uint32_t count;  // ops (global tile) or 8-byte units (local record); kEndItem = stop
+    uint32_t off;    // global tile: index of its first op in the stage (0 or 1)
+    uint32_t local;  // 1 = local record
+    uint32_t pad;
 };
 
 __device__ inline uint32_t find_job(const JobList &jl, uint32_t cta)
@@ -71,6 +71,46 @@ __device__ inline uint64_t *row_ptr(const Job &J, uint32_t ref, uint64_t col)
     return J.S + (uint64_t)ref * J.ld + col;
 }
 
+__device__ inline void consumers_sync() { asm volatile("bar.sync 1, %0;" ::"r"(kConsumers) : "memory"); }
+
+// Barrier of the consumer warps (named barrier 1) that also ORs a predicate
+// across them, so that every consumer takes the same decision to stop.
+__device__ inline bool consumers_sync_or(bool p)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred ip, op;\n\t"
+        "setp.ne.u32 ip, %1, 0;\n\t"
+        "bar.red.or.pred op, 1, %2, ip;\n\t"
+        "selp.u32 %0, 1, 0, op;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)p), "r"(kConsumers)
+        : "memory");
+    return r != 0;
+}
+
+__device__ inline void cp_async16(void *smem_dst, const void *gmem_src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(smem_dst)), "l"(gmem_src) : "memory");
+}
+
+__device__ inline void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+__device__ inline u64x2 lds16(const u64x2 *p)
+{
+    u64x2 r;
+    asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(r.x), "=l"(r.y) : "r"(smem_addr(p)) : "memory");
+    return r;
+}
+
+__device__ inline void sts16(u64x2 *p, u64x2 v)
+{
+    asm volatile("st.shared.v2.u64 [%0], {%1, %2};" ::"r"(smem_addr(p)), "l"(v.x), "l"(v.y) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// global tile: ops name rows by node id and read/write the matrix directly
+// ---------------------------------------------------------------------------
 // PULL: S[x] |= OR of the listed source rows (aux[b] = count, then refs)
 __device__ inline void apply_pull(const Job &J, uint32_t x, uint32_t b, uint64_t col)
 {
@@ -137,29 +177,102 @@ __device__ inline void apply_tile(const Job &J, const uint2 *ops, uint32_t count
     }
 }
 
-// Barrier of the consumer warps (named barrier 1) that also ORs a predicate
-// across them, so that every consumer takes the same decision to stop.
-__device__ inline bool consumers_sync_or(bool p)
+// ---------------------------------------------------------------------------
+// local record: the window's rows are gathered into shared memory, its levels
+// are applied there, and the rows are written back
+// ---------------------------------------------------------------------------
+__device__ inline void apply_record(const Job &J, const uint32_t *rec, u64x2 *buf, uint32_t ct, uint64_t w0)
 {
-    uint32_t r;
-    asm volatile(
-        "{\n\t.reg .pred ip, op;\n\t"
-        "setp.ne.u32 ip, %1, 0;\n\t"
-        "bar.red.or.pred op, 1, %2, ip;\n\t"
-        "selp.u32 %0, 1, 0, op;\n\t}"
-        : "=r"(r)
-        : "r"((uint32_t)p), "r"(kConsumers)
-        : "memory");
-    return r != 0;
+    const uint32_t D = rec[0], nlev = rec[2], nops = rec[3];
+    const uint32_t *rows = rec + 4, *lvl = rows + D, *ops = lvl + nlev + 1, *aux = ops + nops;
+    const uint32_t cpr_log = J.lsw - 1;
+    const uint32_t cpr = 1u << cpr_log;
+    const uint32_t chunk = ct & (cpr - 1u);
+    const uint32_t lane0 = ct >> cpr_log, stride = (uint32_t)kConsumers >> cpr_log;
+    const uint64_t col = w0 + 2ull * chunk;
+    const bool active = col < J.ld;
+    u64x2 *mine = buf + chunk;  // slot q of this chunk lives at buf[q * cpr + chunk]
+
+    if (active) {
+        uint32_t d = lane0;
+        for (; d + 3 * stride < D; d += 4 * stride) {
+            uint32_t r[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) r[k] = rows[d + k * stride];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) cp_async16(mine + (d + k * stride) * cpr, J.S + (uint64_t)r[k] * J.ld + col);
+        }
+        for (; d < D; d += stride) cp_async16(mine + d * cpr, J.S + (uint64_t)rows[d] * J.ld + col);
+    }
+    cp_async_wait_all();
+    consumers_sync();
+    for (uint32_t l = 0; l < nlev; ++l) {
+        if (active) {
+            const uint32_t e = lvl[l + 1];
+            // two ops per step: the ops of one level touch distinct rows, so
+            // both ops' loads can be issued before either op's stores
+            for (uint32_t o = lvl[l] + lane0; o < e; o += 2 * stride) {
+                uint32_t op[2];
+                bool live[2];
+                u64x2 x[2], y[2];
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const uint32_t idx = o + k * stride;
+                    live[k] = idx < e;
+                    op[k] = live[k] ? ops[idx] : (kPull << kKindShift);
+                    const uint32_t kind = op[k] >> kKindShift, a = (op[k] >> 15) & kLocalMask, b = op[k] & kLocalMask;
+                    if (kind != kPull) {
+                        x[k] = lds16(mine + a * cpr);
+                        y[k] = lds16(mine + b * cpr);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const uint32_t kind = op[k] >> kKindShift, a = (op[k] >> 15) & kLocalMask, b = op[k] & kLocalMask;
+                    if (kind == kEvent) {
+                        const u64x2 r = or16(x[k], y[k]);
+                        sts16(mine + a * cpr, r);
+                        sts16(mine + b * cpr, r);
+                    } else if (kind == kOneway) {
+                        sts16(mine + a * cpr, or16(x[k], y[k]));
+                    } else if (kind == kCopy) {
+                        sts16(mine + a * cpr, y[k]);
+                    } else if (live[k]) {
+                        u64x2 acc = lds16(mine + a * cpr);
+                        const uint32_t c = aux[b];
+                        for (uint32_t q = 1; q <= c; ++q) acc = or16(acc, lds16(mine + aux[b + q] * cpr));
+                        sts16(mine + a * cpr, acc);
+                    }
+                }
+            }
+        }
+        consumers_sync();
+    }
+    if (active) {
+        uint32_t d = lane0;
+        for (; d + 3 * stride < D; d += 4 * stride) {
+            u64x2 r[4];
+            uint32_t g[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                r[k] = lds16(mine + (d + k * stride) * cpr);
+                g[k] = rows[d + k * stride];
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) st_row16(J.S + (uint64_t)g[k] * J.ld + col, r[k]);
+        }
+        for (; d < D; d += stride) st_row16(J.S + (uint64_t)rows[d] * J.ld + col, lds16(mine + d * cpr));
+    }
 }
 
-__global__ void __launch_bounds__(kThreads, 2) stream_kernel(const __grid_constant__ JobList jl)
+__global__ void __launch_bounds__(kThreads) stream_kernel(const __grid_constant__ JobList jl)
 {
     extern __shared__ __align__(128) uint8_t smem[];
-    uint2 *stage_ops = reinterpret_cast<uint2 *>(smem);
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + sizeof(uint2) * kStages * kStageOps);
+    uint8_t *stage = smem;  // kStages x kStageBytes
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)kStages * kStageBytes);
     uint64_t *empty = full + kStages;
-    TileHdr *hdr = reinterpret_cast<TileHdr *>(empty + kStages);
+    StageHdr *hdr = reinterpret_cast<StageHdr *>(empty + kStages);
+    u64x2 *rowbuf = reinterpret_cast<u64x2 *>(hdr + kStages);  // 16-byte aligned
     __shared__ uint32_t producer_abort;
     __shared__ int32_t gate;
 
@@ -179,71 +292,78 @@ __global__ void __launch_bounds__(kThreads, 2) stream_kernel(const __grid_consta
     if (gate != 0) return;
 
     if (warp == 0) {
-        // ---------------- producer ----------------
-        uint64_t tile = 0;
+        // ---------------- producer: one bulk copy per item ----------------
+        uint64_t slot = 0;  // stage uses so far
         int ok = 1;
-        for (uint64_t l0 = 0; l0 < J.nlev && ok; l0 += 32) {
-            const uint64_t l = l0 + lane;
-            const uint32_t beg = l < J.nlev ? __ldg(J.lvl + l) : 0u;
-            const uint32_t end = l < J.nlev ? __ldg(J.lvl + l + 1) : 0u;
-            const uint32_t nl = (J.nlev - l0 < 32) ? (uint32_t)(J.nlev - l0) : 32u;
-            for (uint32_t k = 0; k < nl && ok; ++k) {
-                const uint32_t b = __shfl_sync(0xffffffffu, beg, k);
-                const uint32_t e = __shfl_sync(0xffffffffu, end, k);
-                for (uint32_t c = b; c < e && ok; c += kTileOps) {
-                    const uint32_t ce = min(e, c + kTileOps);
-                    const int s = (int)(tile % kStages);
-                    if (lane == 0) {
-                        if (tile >= kStages && !mbar_wait_bounded(&empty[s], (uint32_t)((tile / kStages) - 1) & 1u)) {
-                            record_status(J.status, TN_ETIMEOUT);
-                            producer_abort = 1;
-                            ok = 0;
-                        } else {
-                            const uint32_t a0 = c & ~1u;
-                            const uint32_t bytes = ((ce - a0 + 1u) & ~1u) * (uint32_t)sizeof(uint2);
-                            hdr[s].count = ce - c;
-                            hdr[s].off = c - a0;
-                            mbar_arrive_expect_tx(&full[s], bytes);
-                            bulk_g2s(stage_ops + (size_t)s * kStageOps, J.ops + a0, bytes, &full[s]);
+        for (uint64_t i0 = 0; i0 < J.nitems && ok; i0 += 32) {
+            const uint4 mine = (i0 + lane < J.nitems) ? __ldg(J.items + i0 + lane) : make_uint4(0u, 0u, 0u, 0u);
+            const uint32_t nb = (J.nitems - i0 < 32) ? (uint32_t)(J.nitems - i0) : 32u;
+            for (uint32_t k = 0; k < nb && ok; ++k) {
+                const uint32_t off8 = __shfl_sync(0xffffffffu, mine.x, k);
+                const uint32_t count = __shfl_sync(0xffffffffu, mine.y, k);
+                const uint32_t flags = __shfl_sync(0xffffffffu, mine.z, k);
+                const int s = (int)(slot % kStages);
+                if (lane == 0) {
+                    if (slot >= kStages && !mbar_wait_bounded(&empty[s], (uint32_t)((slot / kStages) - 1) & 1u)) {
+                        record_status(J.status, TN_ETIMEOUT);
+                        producer_abort = 1;
+                        ok = 0;
+                    } else {
+                        uint32_t a0 = off8, n8 = count, off = 0;
+                        if (!(flags & kItemLocal)) {  // global tile: start on a 16-byte boundary
+                            a0 = off8 & ~1u;
+                            off = off8 - a0;
+                            n8 = (count + off + 1u) & ~1u;
                         }
+                        hdr[s].count = count;
+                        hdr[s].off = off;
+                        hdr[s].local = flags & kItemLocal;
+                        mbar_arrive_expect_tx(&full[s], n8 * 8u);
+                        bulk_g2s(stage + (size_t)s * kStageBytes, J.blob + a0, n8 * 8u, &full[s]);
                     }
-                    ok = __shfl_sync(0xffffffffu, ok, 0);
-                    if (ok) ++tile;
                 }
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                if (ok) ++slot;
             }
         }
         if (lane == 0) {
             if (ok) {
-                const int s = (int)(tile % kStages);
-                if (tile >= kStages && !mbar_wait_bounded(&empty[s], (uint32_t)((tile / kStages) - 1) & 1u)) {
+                const int s = (int)(slot % kStages);
+                if (slot >= kStages && !mbar_wait_bounded(&empty[s], (uint32_t)((slot / kStages) - 1) & 1u)) {
                     record_status(J.status, TN_ETIMEOUT);
                     producer_abort = 1;
                 } else {
-                    hdr[s].count = kEndTile;
+                    hdr[s].count = kEndItem;
                     hdr[s].off = 0;
+                    hdr[s].local = 0;
                     mbar_arrive(&full[s]);
-                    ++tile;
+                    ++slot;
                 }
             }
             // no bulk copy may still be writing this CTA's shared memory at exit
-            const uint64_t first = tile > (uint64_t)kStages ? tile - kStages : 0;
-            for (uint64_t q = first; q < tile; ++q)
+            const uint64_t first = slot > (uint64_t)kStages ? slot - kStages : 0;
+            for (uint64_t q = first; q < slot; ++q)
                 mbar_wait_bounded(&full[q % kStages], (uint32_t)(q / kStages) & 1u);
         }
     } else {
         // ---------------- consumers ----------------
         const uint32_t ct = threadIdx.x - 32;
-        for (uint64_t tile = 0;; ++tile) {
-            const int s = (int)(tile % kStages);
-            const uint32_t par = (uint32_t)(tile / kStages) & 1u;
+        for (uint64_t it = 0;; ++it) {
+            const int s = (int)(it % kStages);
+            const uint32_t par = (uint32_t)(it / kStages) & 1u;
             const bool ready = mbar_wait_bounded(&full[s], par);
             if (!ready && ct == 0) record_status(J.status, TN_ETIMEOUT);
             const bool stop = !ready || *(volatile uint32_t *)&producer_abort != 0 ||
-                              (ready && hdr[s].count == kEndTile);
-            // level barrier: the previous tile's stores are ordered before this
-            // tile's loads, and all consumers agree on stopping
+                              (ready && hdr[s].count == kEndItem);
+            // level barrier: the previous item's stores are ordered before this
+            // item's loads, and all consumers agree on stopping
             if (consumers_sync_or(stop)) break;
-            apply_tile(J, stage_ops + (size_t)s * kStageOps + hdr[s].off, hdr[s].count, ct, w0);
+            if (hdr[s].local) {
+                apply_record(J, reinterpret_cast<const uint32_t *>(stage + (size_t)s * kStageBytes), rowbuf, ct, w0);
+            } else {
+                apply_tile(J, reinterpret_cast<const uint2 *>(stage + (size_t)s * kStageBytes) + hdr[s].off,
+                           hdr[s].count, ct, w0);
+            }
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);
         }
@@ -346,12 +466,7 @@ tn_status apply_jobs(const tn_plan *const *plans, uint64_t *const *S, const uint
         // the identity initialisation needs one column per node
         if ((flags & TN_INIT_IDENTITY) && !src[i] && ncols[i] != p->n) return TN_EINVAL;
     }
-    static bool attr_set = false;
-    const size_t smem = sizeof(uint2) * kStages * kStageOps + 2 * kStages * sizeof(uint64_t) + kStages * sizeof(TileHdr);
-    if (!attr_set) {
-        TN_CUDA_TRY(cudaFuncSetAttribute(stream_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr_set = true;
-    }
+    const size_t smem_base = (size_t)kStages * kStageBytes + 2 * kStages * sizeof(uint64_t) + kStages * sizeof(StageHdr);
     uint64_t *tmps[kMaxJobs];
     for (uint32_t base = 0; base < count; base += kMaxJobs) {
         const uint32_t nj = count - base < (uint32_t)kMaxJobs ? count - base : (uint32_t)kMaxJobs;
@@ -359,6 +474,7 @@ tn_status apply_jobs(const tn_plan *const *plans, uint64_t *const *S, const uint
         memset(&jl, 0, sizeof(jl));
         jl.count = nj;
         uint32_t ctas = 0;
+        size_t smem = smem_base;
         for (uint32_t j = 0; j < nj; ++j) {
             const uint32_t i = base + j;
             const tn_plan *p = plans[i];
@@ -381,13 +497,14 @@ tn_status apply_jobs(const tn_plan *const *plans, uint64_t *const *S, const uint
                 }
             }
             if (p->temps) TN_CUDA_TRY(cudaMallocAsync((void **)&tmps[j], p->temps * ld * sizeof(uint64_t), st));
-            uint32_t sw = p->slab_words ? p->slab_words : 4u;
-            while ((uint64_t)sw > ld && sw > 2) sw >>= 1;
+            const uint32_t sw = p->slab_words;
+            const size_t need = smem_base + (size_t)p->dcap * sw * 8;
+            if (need > smem) smem = need;
             Job &J = jl.job[j];
-            J.ops = p->d_ops;
-            J.lvl = p->d_lvl;
+            J.blob = p->d_blob;
+            J.items = p->d_items;
             J.aux = p->d_aux;
-            J.nlev = p->levels;
+            J.nitems = p->items;
             J.S = S[i];
             J.ld = ld;
             J.tmp = tmps[j];
@@ -399,6 +516,7 @@ tn_status apply_jobs(const tn_plan *const *plans, uint64_t *const *S, const uint
         }
         TN_CUDA_TRY(cudaGetLastError());
         if (ctas) {
+            TN_CUDA_TRY(cudaFuncSetAttribute(stream_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             tn_internal_count_launches(1);
             stream_kernel<<<ctas, kThreads, smem, st>>>(jl);
         }

@@ -41,6 +41,28 @@ constexpr uint32_t kNoRef = 0xFFFFFFFFu;  // empty slot in a batch of source ref
 
 __host__ __device__ inline uint32_t op_a(uint32_t kind, uint32_t id) { return (kind << kKindShift) | id; }
 
+// Work items of the streaming kernel.  The planner emits one item per window
+// whose rows fit the kernel's shared-memory row buffer (a "local record") and
+// one item per tile of ops for the other windows ("global tiles").  Items are
+// copied whole into one shared-memory staging buffer of kStageBytes.
+//   local record (uint32 words): D, T, nlev, nops | rows[D] (node ids) |
+//     lvl[nlev + 1] (op offsets) | ops[nops] | aux[...] | zero padding to 16 B.
+//     Rows are named by local slots: 0..D-1 the window's rows, D..D+T-1 saved
+//     copies.  op = kind << 30 | a << 15 | b  (PULL: b = aux offset).
+//   global tile: uint2 ops as above (node ids, absolute aux indices).
+// item = {offset in 8-byte units, count (global: ops; local: 8-byte units), flags, 0}
+constexpr uint32_t kStageBytes = 16384;
+constexpr uint32_t kTileOps = kStageBytes / 8 - 2;
+constexpr uint32_t kItemLocal = 1u;
+constexpr uint32_t kItemLevelEnd = 2u;
+constexpr uint32_t kLocalMask = 0x7FFFu;
+constexpr uint32_t kLocalSlotLimit = 0x7FFFu;
+
+__host__ __device__ inline uint32_t local_op(uint32_t kind, uint32_t a, uint32_t b)
+{
+    return (kind << kKindShift) | (a << 15) | b;
+}
+
 __device__ inline void record_status(int32_t *status, int32_t code)
 {
     if (status) atomicCAS(status, 0, code);
@@ -191,14 +213,15 @@ struct tn_plan {
     int device;
     uint64_t m;
     uint32_t n;
-    uint64_t windows, levels, ops, aux, temps, big_windows;
+    uint64_t windows, levels, ops, aux, temps, big_windows, local_windows, items, blob8;
     int64_t t_first, t_last;
-    uint32_t slab_words; // words of every row owned by one CTA when applied (0 = default)
-    uint2 *d_ops;        // [ops]        level-ordered row operations
-    uint32_t *d_lvl;     // [levels + 1] op offset of every level
-    uint32_t *d_aux;     // [aux]        source lists of PULL ops
-    int64_t *d_tbounds;  // [2]          t_first, t_last
-    int32_t *d_status;   // [1]          first asynchronous error
+    uint32_t slab_words;  // 64-bit words of every row owned by one CTA
+    uint32_t dcap;        // row slots of the kernel's shared-memory row buffer
+    uint2 *d_blob;        // [blob8 + 2]  item payloads (8-byte units)
+    uint4 *d_items;       // [items]      work items in execution order
+    uint32_t *d_aux;      // [aux]        source lists of global PULL ops
+    int64_t *d_tbounds;   // [2]          t_first, t_last
+    int32_t *d_status;    // [1]          first asynchronous error
 };
 
 namespace tn {

@@ -40,7 +40,10 @@
 namespace tn {
 
 constexpr int kPlanThreads = 256;
-constexpr uint32_t kDefaultWindow = 2048;
+constexpr uint32_t kDefaultWindow = 640;
+constexpr uint32_t kDefaultSlab = 16;
+constexpr uint32_t kRowBufferBytes = 160 * 1024;  // default shared-memory row buffer of the streaming kernel
+constexpr uint32_t kWinFields = 8;  // nops, nlev, naux, ntemp, local, blob8, nitems, all ops
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 
@@ -51,7 +54,7 @@ constexpr uint32_t kFlagShA = 1u << 30;
 constexpr uint32_t kFlagShB = 1u << 31;
 
 // arena layout (uint32 words) for a window of E events:
-//   lu[E] lv[E] grp[E] evl[E] run_node[E] run_aux[E] run_lev[E] run_temp[E] scratch[3*Hs]
+//   lu[E] lv[E] grp[E] evl[E] run_node[E] run_aux[E] run_lev[E] run_temp[E] rowsg[2E] scratch
 // scratch: hash keys + ids (2*H words, H = hash slots) during id assignment,
 // then node state nlev/ncnt/nrun (3*D words, D <= 2E distinct nodes), then the
 // level histogram (<= 2E + 3 words).
@@ -62,7 +65,7 @@ __host__ __device__ inline uint64_t arena_words(uint64_t E)
     uint64_t scratch = 2 * H;
     if (6 * E > scratch) scratch = 6 * E;
     if (2 * E + 3 > scratch) scratch = 2 * E + 3;
-    return 8 * E + scratch;
+    return 10 * E + scratch;
 }
 
 struct PlanArgs {
@@ -75,12 +78,15 @@ struct PlanArgs {
     uint32_t nw;         // number of windows
     uint64_t *wstart;    // [nw + 1]
     uint32_t smem_max_events;
-    // per-window results: nops, nlev, naux, ntemp
-    uint32_t *wcount;    // [4 * nw]
-    // staging (window w uses the regions starting at 3*s_w / 2*s_w + w)
+    uint32_t dcap;          // row slots of a local window
+    uint32_t max_rec_words; // largest local record (words)
+    // per-window results (kWinFields each)
+    uint32_t *wcount;    // [kWinFields * nw]
+    // staging (window w uses the regions starting at 3*s_w / 2*s_w + w / 10*s_w + 8*w)
     uint2 *ops_stage;    // [3m]
     uint32_t *aux_stage; // [3m]
     uint32_t *lvl_stage; // [2m + nw + 1]
+    uint32_t *rec_stage; // [10m + 8nw]
     // large windows
     uint32_t *big_list;  // [nw]
     uint64_t *big_off;   // [nw]
@@ -183,28 +189,26 @@ __device__ void schedule_window(const PlanArgs &a, uint32_t w, uint32_t *arena)
 {
     __shared__ uint32_t warp_sums[32];
     __shared__ uint32_t tot;
-    __shared__ uint32_t res[5];  // nops, nlev(maxlev), naux, ntemp, nruns
+    __shared__ uint32_t res[8];  // nops, maxlev, naux, ntemp, nruns, local, nitems
 
     const uint64_t s = a.wstart[w];
     const uint32_t E = (uint32_t)(a.wstart[w + 1] - s);
-    uint32_t *cnt = a.wcount + 4ull * w;
+    uint32_t *cnt = a.wcount + (uint64_t)kWinFields * w;
     if (E == 0) {
-        if (threadIdx.x == 0) {
-            cnt[0] = cnt[1] = cnt[2] = cnt[3] = 0;
-            a.lvl_stage[2 * s + w] = 0;
-        }
+        if (threadIdx.x < kWinFields) cnt[threadIdx.x] = 0;
         return;
     }
     const uint32_t T = blockDim.x, tid = threadIdx.x;
     const uint32_t H = (uint32_t)hash_slots(E);
     uint32_t *lu = arena, *lv = lu + E, *grp = lv + E, *evl = grp + E;
     uint32_t *run_node = evl + E, *run_aux = run_node + E, *run_lev = run_aux + E, *run_temp = run_lev + E;
-    uint32_t *scratch = run_temp + E;
+    uint32_t *rowsg = run_temp + E;  // [2E] global id of every local row id
+    uint32_t *scratch = rowsg + 2 * E;
     uint32_t *hkey = scratch, *hval = scratch + H;
     const uint32_t *U = a.u + s, *V = a.v + s;
     const int64_t *Tt = a.t + s;
 
-    // 1. compact node ids
+    // 1. compact node ids (local row ids 0..D-1)
     for (uint32_t i = tid; i < H; i += T) hkey[i] = kEmpty;
     __syncthreads();
     for (uint32_t i = tid; i < E; i += T) {
@@ -215,6 +219,8 @@ __device__ void schedule_window(const PlanArgs &a, uint32_t w, uint32_t *arena)
     for (uint32_t i = tid; i < H; i += T) hval[i] = hkey[i] != kEmpty ? 1u : 0u;
     __syncthreads();
     const uint32_t D = block_excl_scan_array(hval, H, warp_sums, &tot);
+    for (uint32_t i = tid; i < H; i += T)
+        if (hkey[i] != kEmpty) rowsg[hval[i]] = hkey[i];
     for (uint32_t i = tid; i < E; i += T) {
         lu[i] = hlookup(hkey, hval, H, U[i]);
         lv[i] = hlookup(hkey, hval, H, V[i]);
@@ -233,7 +239,8 @@ __device__ void schedule_window(const PlanArgs &a, uint32_t w, uint32_t *arena)
     }
     __syncthreads();
 
-    // 2. sequential level scan (one thread), in time order
+    // 2. sequential level scan (one thread), in time order.  Rows are named by
+    //    local ids here; PULL source lists hold local ids or temp references.
     if (tid == 0) {
         uint32_t nruns = 0, naux = 0, ntemp = 0, maxlev = 0;
         uint32_t *auxw = a.aux_stage + 3 * s;
@@ -295,7 +302,7 @@ __device__ void schedule_window(const PlanArgs &a, uint32_t w, uint32_t *arena)
                         if (rx == kNone) {
                             rx = nruns++;
                             nrun[x] = rx;
-                            run_node[rx] = U[j];
+                            run_node[rx] = x;
                             run_aux[rx] = naux;
                             run_lev[rx] = 0;  // fill counter until the level is known
                             run_temp[rx] = kNone;
@@ -308,7 +315,7 @@ __device__ void schedule_window(const PlanArgs &a, uint32_t w, uint32_t *arena)
                         if (ry == kNone) {
                             ry = nruns++;
                             nrun[y] = ry;
-                            run_node[ry] = V[j];
+                            run_node[ry] = y;
                             run_aux[ry] = naux;
                             run_lev[ry] = 0;
                             run_temp[ry] = kNone;
@@ -322,9 +329,9 @@ __device__ void schedule_window(const PlanArgs &a, uint32_t w, uint32_t *arena)
                         auxw[run_aux[rx] + 1 + run_lev[rx]++] = kTempRef | run_temp[ry];
                         auxw[run_aux[ry] + 1 + run_lev[ry]++] = kTempRef | run_temp[rx];
                     } else if (sx) {
-                        auxw[run_aux[rx] + 1 + run_lev[rx]++] = V[j];
+                        auxw[run_aux[rx] + 1 + run_lev[rx]++] = y;
                     } else {
-                        auxw[run_aux[ry] + 1 + run_lev[ry]++] = U[j];
+                        auxw[run_aux[ry] + 1 + run_lev[ry]++] = x;
                     }
                 }
                 if (any) {
@@ -342,14 +349,14 @@ __device__ void schedule_window(const PlanArgs &a, uint32_t w, uint32_t *arena)
             }
             i = g1;
         }
-        res[0] = 0;
         res[1] = maxlev;
         res[2] = naux;
         res[3] = ntemp;
         res[4] = nruns;
+        res[6] = 0;
     }
     __syncthreads();
-    const uint32_t maxlev = res[1], nruns = res[4];
+    const uint32_t maxlev = res[1], naux = res[2], ntemp = res[3], nruns = res[4];
 
     // 3. counting sort of the updates by level (levels 1..maxlev -> 0..maxlev-1)
     uint32_t *lh = scratch;  // node state is dead
@@ -371,8 +378,81 @@ __device__ void schedule_window(const PlanArgs &a, uint32_t w, uint32_t *arena)
     }
     __syncthreads();
     const uint32_t nops = block_excl_scan_array(lh, maxlev + 1, warp_sums, &tot);
+
+    // 4. mode: the window's rows and saved rows fit the streaming kernel's
+    //    shared-memory row buffer, and its record fits one staging buffer
+    const uint32_t rec_words = 4 + D + (maxlev + 1) + nops + naux;
+    const uint32_t rec_words_pad = (rec_words + 3u) & ~3u;
+    const bool local = D + ntemp <= a.dcap && rec_words_pad <= a.max_rec_words;
+
+    if (local) {
+        // record: header | rows[D] | lvl[maxlev+1] | ops[nops] | aux[naux] | pad
+        uint32_t *rec = a.rec_stage + 10 * s + 8ull * w;
+        uint32_t *rrows = rec + 4, *rlvl = rrows + D, *rops = rlvl + maxlev + 1, *raux = rops + nops;
+        if (tid == 0) {
+            rec[0] = D;
+            rec[1] = ntemp;
+            rec[2] = maxlev;
+            rec[3] = nops;
+        }
+        for (uint32_t d = tid; d < D; d += T) rrows[d] = rowsg[d];
+        for (uint32_t j = tid; j < maxlev + 1; j += T) rlvl[j] = lh[j];
+        for (uint32_t k = rec_words + tid; k < rec_words_pad; k += T) rec[k] = 0;
+        const uint32_t *auxw = a.aux_stage + 3 * s;
+        for (uint32_t r = tid; r < nruns; r += T) {
+            const uint32_t b = run_aux[r], c = auxw[b];
+            raux[b] = c;
+            for (uint32_t q = 1; q <= c; ++q) {
+                const uint32_t ref = auxw[b + q];
+                raux[b + q] = (ref & kTempRef) ? D + (ref & ~kTempRef) : ref;
+            }
+        }
+        __syncthreads();
+        for (uint32_t i = tid; i < E; i += T) {
+            const uint32_t f = grp[i];
+            if (f & kFlagNoop) continue;
+            const uint32_t x = lu[i], y = lv[i];
+            const uint32_t L = evl[i] - 1;
+            if (f & kFlagIso) {
+                rops[atomicAdd(&lh[L], 1u)] = local_op(kEvent, x, y);
+            } else {
+                if (!(f & kFlagShA)) rops[atomicAdd(&lh[L], 1u)] = local_op(kOneway, x, y);
+                if (!(f & kFlagShB)) rops[atomicAdd(&lh[L], 1u)] = local_op(kOneway, y, x);
+            }
+        }
+        for (uint32_t r = tid; r < nruns; r += T) {
+            const uint32_t L = run_lev[r];
+            rops[atomicAdd(&lh[L], 1u)] = local_op(kPull, run_node[r], run_aux[r]);
+            if (run_temp[r] != kNone) rops[atomicAdd(&lh[L - 1], 1u)] = local_op(kCopy, D + run_temp[r], run_node[r]);
+        }
+        if (tid == 0) {
+            cnt[0] = 0;
+            cnt[1] = maxlev;
+            cnt[2] = 0;
+            cnt[3] = 0;
+            cnt[4] = 1;
+            cnt[5] = rec_words_pad / 2;
+            cnt[6] = 1;
+            cnt[7] = nops;
+        }
+        return;
+    }
+
+    // global mode: ops name rows by node id; PULL lists are converted in place
     uint32_t *lvl_out = a.lvl_stage + 2 * s + w;
     for (uint32_t j = tid; j < maxlev + 1; j += T) lvl_out[j] = lh[j];
+    for (uint32_t j = tid; j < maxlev; j += T) {
+        const uint32_t c = lh[j + 1] - lh[j];
+        atomicAdd(&res[6], (c + kTileOps - 1) / kTileOps);
+    }
+    uint32_t *auxw = a.aux_stage + 3 * s;
+    for (uint32_t r = tid; r < nruns; r += T) {
+        const uint32_t b = run_aux[r], c = auxw[b];
+        for (uint32_t q = 1; q <= c; ++q) {
+            const uint32_t ref = auxw[b + q];
+            if (!(ref & kTempRef)) auxw[b + q] = rowsg[ref];
+        }
+    }
     __syncthreads();
     uint2 *ops = a.ops_stage + 3 * s;
     for (uint32_t i = tid; i < E; i += T) {
@@ -388,16 +468,20 @@ __device__ void schedule_window(const PlanArgs &a, uint32_t w, uint32_t *arena)
         }
     }
     for (uint32_t r = tid; r < nruns; r += T) {
-        const uint32_t L = run_lev[r];
-        ops[atomicAdd(&lh[L], 1u)] = make_uint2(op_a(kPull, run_node[r]), (uint32_t)(3 * s) + run_aux[r]);
-        if (run_temp[r] != kNone)
-            ops[atomicAdd(&lh[L - 1], 1u)] = make_uint2(op_a(kCopy, run_temp[r]), run_node[r]);
+        const uint32_t L = run_lev[r], xg = rowsg[run_node[r]];
+        ops[atomicAdd(&lh[L], 1u)] = make_uint2(op_a(kPull, xg), (uint32_t)(3 * s) + run_aux[r]);
+        if (run_temp[r] != kNone) ops[atomicAdd(&lh[L - 1], 1u)] = make_uint2(op_a(kCopy, run_temp[r]), xg);
     }
+    __syncthreads();
     if (tid == 0) {
         cnt[0] = nops;
         cnt[1] = maxlev;
-        cnt[2] = res[2];
-        cnt[3] = res[3];
+        cnt[2] = naux;
+        cnt[3] = ntemp;
+        cnt[4] = 0;
+        cnt[5] = (nops + 1u) & ~1u;
+        cnt[6] = res[6];
+        cnt[7] = nops;
     }
 }
 
@@ -420,60 +504,90 @@ __global__ void __launch_bounds__(kPlanThreads) schedule_big_kernel(PlanArgs a)
 // concatenation of the windows
 // ---------------------------------------------------------------------------
 struct Totals {
-    unsigned long long nops, nlev, naux, tmax;
+    unsigned long long items, blob8, naux, tmax, levels, ops, local;
 };
 
-// exclusive scans of nops / nlev / naux over windows (one CTA)
-__global__ void window_scan_kernel(uint32_t *wcount, uint32_t nw, uint64_t *base /* [3*nw] */, Totals *tot)
+// exclusive scans over windows of nitems / blob8 / naux (one CTA)
+__global__ void window_scan_kernel(const uint32_t *wcount, uint32_t nw, uint64_t *base /* [3*nw] */, Totals *tot)
 {
     __shared__ uint32_t warp_sums[32];
     __shared__ uint32_t total;
     __shared__ unsigned long long carry[3];
+    __shared__ unsigned long long levels, ops, local;
     __shared__ unsigned int tmax;
     if (threadIdx.x < 3) carry[threadIdx.x] = 0;
-    if (threadIdx.x == 0) tmax = 0;
+    if (threadIdx.x == 0) {
+        tmax = 0;
+        levels = ops = local = 0;
+    }
     __syncthreads();
+    const int field[3] = {6, 5, 2};
     for (uint32_t c0 = 0; c0 < nw; c0 += blockDim.x) {
         const uint32_t w = c0 + threadIdx.x;
+        const uint32_t *c = wcount + (uint64_t)kWinFields * w;
         for (int k = 0; k < 3; ++k) {
-            uint32_t x = w < nw ? wcount[4 * w + k] : 0u;
+            uint32_t x = w < nw ? c[field[k]] : 0u;
             uint32_t ex = block_excl_scan_value(x, warp_sums, &total);
             if (w < nw) base[3ull * w + k] = carry[k] + ex;
             __syncthreads();
             if (threadIdx.x == 0) carry[k] += total;
             __syncthreads();
         }
-        if (w < nw) atomicMax(&tmax, wcount[4 * w + 3]);
+        if (w < nw) {
+            atomicMax(&tmax, c[3]);
+            atomicAdd(&levels, (unsigned long long)c[1]);
+            atomicAdd(&ops, (unsigned long long)c[7]);
+            atomicAdd(&local, (unsigned long long)c[4]);
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        tot->nops = carry[0];
-        tot->nlev = carry[1];
+        tot->items = carry[0];
+        tot->blob8 = carry[1];
         tot->naux = carry[2];
         tot->tmax = tmax;
+        tot->levels = levels;
+        tot->ops = ops;
+        tot->local = local;
     }
 }
 
-__global__ void compact_kernel(const uint64_t *wstart, const uint32_t *wcount, const uint64_t *base, uint32_t nw,
-                               const uint2 *ops_stage, const uint32_t *aux_stage, const uint32_t *lvl_stage,
-                               uint2 *ops, uint32_t *aux, uint32_t *lvl, uint64_t total_ops, uint64_t total_lev)
+// concatenation of the windows into the blob, the item list and the aux list
+__global__ void compact_kernel(PlanArgs a, const uint64_t *base, uint2 *blob, uint4 *items, uint32_t *aux)
 {
     const uint32_t w = blockIdx.x;
-    if (w >= nw) return;
-    const uint64_t s = wstart[w];
-    const uint32_t nops = wcount[4 * w], nlev = wcount[4 * w + 1], naux = wcount[4 * w + 2];
-    const uint64_t ob = base[3ull * w], lb = base[3ull * w + 1], ab = base[3ull * w + 2];
-    const uint2 *os = ops_stage + 3 * s;
+    if (w >= a.nw) return;
+    const uint64_t s = a.wstart[w];
+    const uint32_t *c = a.wcount + (uint64_t)kWinFields * w;
+    const uint64_t ib = base[3ull * w], bb = base[3ull * w + 1], ab = base[3ull * w + 2];
+    if (c[4]) {
+        // local record, copied as 8-byte units
+        const uint2 *src = reinterpret_cast<const uint2 *>(a.rec_stage + 10 * s + 8ull * w);
+        for (uint32_t k = threadIdx.x; k < c[5]; k += blockDim.x) blob[bb + k] = src[k];
+        if (threadIdx.x == 0) items[ib] = make_uint4((uint32_t)bb, c[5], kItemLocal, 0u);
+        return;
+    }
+    const uint32_t nops = c[0], nlev = c[1], naux = c[2];
+    if (nops == 0) return;
+    const uint2 *os = a.ops_stage + 3 * s;
     for (uint32_t k = threadIdx.x; k < nops; k += blockDim.x) {
         uint2 op = os[k];
         if ((op.x >> kKindShift) == kPull) op.y = (uint32_t)(op.y - 3 * s + ab);
-        ops[ob + k] = op;
+        blob[bb + k] = op;
     }
-    const uint32_t *as = aux_stage + 3 * s;
+    const uint32_t *as = a.aux_stage + 3 * s;
     for (uint32_t k = threadIdx.x; k < naux; k += blockDim.x) aux[ab + k] = as[k];
-    const uint32_t *ls = lvl_stage + 2 * s + w;
-    for (uint32_t j = threadIdx.x; j < nlev; j += blockDim.x) lvl[lb + j] = (uint32_t)(ob + ls[j]);
-    if (w == 0 && threadIdx.x == 0) lvl[total_lev] = (uint32_t)total_ops;
+    if (threadIdx.x == 0) {
+        const uint32_t *ls = a.lvl_stage + 2 * s + w;
+        uint64_t it = ib;
+        for (uint32_t l = 0; l < nlev; ++l) {
+            const uint32_t b = ls[l], e = ls[l + 1];
+            for (uint32_t q = b; q < e; q += kTileOps) {
+                const uint32_t qe = min(e, q + kTileOps);
+                items[it++] = make_uint4((uint32_t)(bb + q), qe - q, qe == e ? kItemLevelEnd : 0u, 0u);
+            }
+        }
+    }
 }
 
 __global__ void tbounds_kernel(const int64_t *t, uint64_t m, int64_t *out)
@@ -518,16 +632,21 @@ extern "C" tn_status tn_plan_create(const uint32_t *u, const uint32_t *v, const 
     if (!plan_out) return TN_EINVAL;
     *plan_out = nullptr;
     if (!u || !v || !t || m == 0 || n == 0 || n >= (1u << 30) || m >= (1ull << 30)) return TN_EINVAL;
+    uint32_t sw = kDefaultSlab, window = kDefaultWindow, rows = 0;
     if (opt) {
-        for (int i = 0; i < 6; ++i)
+        for (int i = 0; i < 5; ++i)
             if (opt->reserved[i]) return TN_EINVAL;
-        const uint32_t sw = opt->slab_words;
-        if (sw != 0 && sw != 2 && sw != 4 && sw != 8 && sw != 16) return TN_EINVAL;
+        if (opt->slab_words) sw = opt->slab_words;
+        if (opt->window_events) window = opt->window_events;
+        rows = opt->smem_rows;
     }
+    if (sw != 2 && sw != 4 && sw != 8 && sw != 16) return TN_EINVAL;
+    if (window < 32) window = 32;
+    if (rows == 0) rows = kRowBufferBytes / (sw * 8);
+    if (rows > kLocalSlotLimit) rows = kLocalSlotLimit;
+    if ((uint64_t)rows * sw * 8 > 160 * 1024) return TN_EINVAL;  // row buffer must fit the kernel's shared memory
     cudaStream_t st = (cudaStream_t)stream;
     tn_internal_keep_pool();
-    uint32_t window = (opt && opt->window_events) ? opt->window_events : kDefaultWindow;
-    if (window < 32) window = 32;
 
     PlanArgs a;
     memset(&a, 0, sizeof(a));
@@ -540,6 +659,8 @@ extern "C" tn_status tn_plan_create(const uint32_t *u, const uint32_t *v, const 
     a.window = window;
     a.nw = (uint32_t)((m + window - 1) / window);
     a.smem_max_events = smem_max_events();
+    a.dcap = rows;
+    a.max_rec_words = kStageBytes / 4;
 
     tn_plan *p = (tn_plan *)calloc(1, sizeof(tn_plan));
     if (!p) return TN_ENOMEM;
@@ -547,11 +668,13 @@ extern "C" tn_status tn_plan_create(const uint32_t *u, const uint32_t *v, const 
     p->m = m;
     p->n = n;
     p->windows = a.nw;
-    p->slab_words = opt ? opt->slab_words : 0;
+    p->slab_words = sw;
+    p->dcap = rows;
 
     tn_status rc = TN_OK;
     unsigned long long host_counters[4] = {0, 0, 0, 0};
-    Totals host_tot = {0, 0, 0, 0};
+    Totals host_tot;
+    memset(&host_tot, 0, sizeof(host_tot));
     uint64_t *base = nullptr;
     Totals *d_tot = nullptr;
     const int vblocks = (int)((m + 255) / 256 < 4096 ? (m + 255) / 256 : 4096);
@@ -566,15 +689,13 @@ extern "C" tn_status tn_plan_create(const uint32_t *u, const uint32_t *v, const 
 
     TN_STEP(alloc_async(&a.counters, 4, st));
     TN_STEP(alloc_async(&a.wstart, (uint64_t)a.nw + 1, st));
-    TN_STEP(alloc_async(&a.wcount, 4ull * a.nw, st));
+    TN_STEP(alloc_async(&a.wcount, (uint64_t)kWinFields * a.nw, st));
     TN_STEP(alloc_async(&a.big_list, (uint64_t)a.nw, st));
     TN_STEP(alloc_async(&a.big_off, (uint64_t)a.nw, st));
     TN_STEP(cudaMemsetAsync(a.counters, 0, 4 * sizeof(unsigned long long), st));
-    tn_internal_count_launches(1);
+    tn_internal_count_launches(3);
     validate_kernel<<<vblocks, 256, 0, st>>>(a);
-    tn_internal_count_launches(1);
     window_kernel<<<wblocks, 256, 0, st>>>(a);
-    tn_internal_count_launches(1);
     big_window_kernel<<<wblocks, 256, 0, st>>>(a);
     TN_STEP(cudaGetLastError());
     TN_STEP(cudaMemcpyAsync(host_counters, a.counters, sizeof(host_counters), cudaMemcpyDeviceToHost, st));
@@ -592,6 +713,7 @@ extern "C" tn_status tn_plan_create(const uint32_t *u, const uint32_t *v, const 
     TN_STEP(alloc_async(&a.ops_stage, 3 * m, st));
     TN_STEP(alloc_async(&a.aux_stage, 3 * m, st));
     TN_STEP(alloc_async(&a.lvl_stage, 2 * m + a.nw + 1, st));
+    TN_STEP(alloc_async(&a.rec_stage, 10 * m + 8ull * a.nw, st));
     TN_STEP(alloc_async(&a.big_arena, host_counters[2], st));
     {
         const size_t smem = arena_words(host_counters[3] ? host_counters[3] : 1) * 4;
@@ -612,20 +734,21 @@ extern "C" tn_status tn_plan_create(const uint32_t *u, const uint32_t *v, const 
     TN_STEP(cudaMemcpyAsync(&host_tot, d_tot, sizeof(Totals), cudaMemcpyDeviceToHost, st));
     TN_STEP(cudaStreamSynchronize(st));
 
-    p->levels = host_tot.nlev;
-    p->ops = host_tot.nops;
+    p->items = host_tot.items;
+    p->blob8 = host_tot.blob8;
     p->aux = host_tot.naux;
     p->temps = host_tot.tmax;
-    TN_STEP(alloc_async(&p->d_ops, p->ops + 2, st));  // bulk copies may read one op past a level
-    TN_STEP(alloc_async(&p->d_lvl, p->levels + 1, st));
+    p->levels = host_tot.levels;
+    p->ops = host_tot.ops;
+    p->local_windows = host_tot.local;
+    TN_STEP(alloc_async(&p->d_blob, p->blob8 + 2, st));  // a global tile may read one op past its end
+    TN_STEP(alloc_async(&p->d_items, p->items > 0 ? p->items : 1, st));
     TN_STEP(alloc_async(&p->d_aux, p->aux > 0 ? p->aux : 1, st));
     TN_STEP(alloc_async(&p->d_tbounds, 2, st));
     TN_STEP(alloc_async(&p->d_status, 1, st));
     TN_STEP(cudaMemsetAsync(p->d_status, 0, sizeof(int32_t), st));
-    tn_internal_count_launches(1);
-    compact_kernel<<<a.nw, 256, 0, st>>>(a.wstart, a.wcount, base, a.nw, a.ops_stage, a.aux_stage, a.lvl_stage,
-                                         p->d_ops, p->d_aux, p->d_lvl, p->ops, p->levels);
-    tn_internal_count_launches(1);
+    tn_internal_count_launches(2);
+    compact_kernel<<<a.nw, 256, 0, st>>>(a, base, p->d_blob, p->d_items, p->d_aux);
     tbounds_kernel<<<1, 1, 0, st>>>(t, m, p->d_tbounds);
     TN_STEP(cudaGetLastError());
     {
@@ -650,12 +773,13 @@ done:
     if (a.ops_stage) cudaFreeAsync(a.ops_stage, st);
     if (a.aux_stage) cudaFreeAsync(a.aux_stage, st);
     if (a.lvl_stage) cudaFreeAsync(a.lvl_stage, st);
+    if (a.rec_stage) cudaFreeAsync(a.rec_stage, st);
     if (a.big_arena) cudaFreeAsync(a.big_arena, st);
     if (base) cudaFreeAsync(base, st);
     if (d_tot) cudaFreeAsync(d_tot, st);
     if (rc != TN_OK) {
-        if (p->d_ops) cudaFreeAsync(p->d_ops, st);
-        if (p->d_lvl) cudaFreeAsync(p->d_lvl, st);
+        if (p->d_blob) cudaFreeAsync(p->d_blob, st);
+        if (p->d_items) cudaFreeAsync(p->d_items, st);
         if (p->d_aux) cudaFreeAsync(p->d_aux, st);
         if (p->d_tbounds) cudaFreeAsync(p->d_tbounds, st);
         if (p->d_status) cudaFreeAsync(p->d_status, st);
@@ -671,8 +795,8 @@ extern "C" tn_status tn_plan_destroy(tn_plan *p, void *stream)
 {
     if (!p) return TN_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
-    cudaFreeAsync(p->d_ops, st);
-    cudaFreeAsync(p->d_lvl, st);
+    cudaFreeAsync(p->d_blob, st);
+    cudaFreeAsync(p->d_items, st);
     cudaFreeAsync(p->d_aux, st);
     cudaFreeAsync(p->d_tbounds, st);
     cudaFreeAsync(p->d_status, st);
@@ -691,6 +815,8 @@ extern "C" tn_status tn_plan_get_stats(const tn_plan *p, tn_plan_stats *s)
     s->aux = p->aux;
     s->temps = p->temps;
     s->big_windows = p->big_windows;
+    s->local_windows = p->local_windows;
+    s->items = p->items;
     s->t_first = p->t_first;
     s->t_last = p->t_last;
     return TN_OK;

@@ -74,7 +74,8 @@ def test_fuzz_dense_ties(seed):
     t = np.sort(rng.integers(0, int(rng.integers(1, 12)), m))
     win = int(rng.choice([32, 64, 2048]))
     du, dv, dt = dev_events(u, v, t)
-    plan = tn.Plan(du, dv, dt, n, window_events=win, slab_words=int(rng.choice([2, 4, 8, 16])))
+    plan = tn.Plan(du, dv, dt, n, window_events=win, slab_words=int(rng.choice([2, 4, 8, 16])),
+                   smem_rows=int(rng.choice([0, 1, 64])))
     S = torch.empty((n, tn.tn_row_words(n)), dtype=torch.int64, device="cuda")
     plan.apply(S, init=True)
     assert plan.status() == 0
@@ -107,6 +108,25 @@ def test_schedule_options_identical(slab, window):
     u, v, t = synth.uniform_events(n, 31_001, t_range=12_000, seed=3)
     du, dv, dt = dev_events(u, v, t)
     plan = tn.Plan(du, dv, dt, n, window_events=window, slab_words=slab)
+    S = torch.empty((n, tn.tn_row_words(n)), dtype=torch.int64, device="cuda")
+    plan.apply(S, init=True)
+    assert plan.status() == 0
+    assert np.array_equal(host_matrix(S, n), oracle.component_matrix(u, v, t, n))
+
+
+@pytest.mark.parametrize("smem_rows", [1, 0, 2000])
+def test_local_and_global_windows_identical(smem_rows):
+    """smem_rows=1 sends every window through the global-memory path; the
+    default and a large buffer apply most windows in shared memory."""
+    n = 5000
+    u, v, t = synth.uniform_events(n, 60_000, t_range=25_000, seed=14)
+    du, dv, dt = dev_events(u, v, t)
+    plan = tn.Plan(du, dv, dt, n, window_events=300, slab_words=8, smem_rows=smem_rows)
+    st = plan.stats()
+    if smem_rows == 1:
+        assert st["local_windows"] == 0
+    else:
+        assert st["local_windows"] > 0
     S = torch.empty((n, tn.tn_row_words(n)), dtype=torch.int64, device="cuda")
     plan.apply(S, init=True)
     assert plan.status() == 0

@@ -42,10 +42,10 @@ def test_exports_every_declared_symbol(lib_path):
 
 def test_host_helpers_without_gpu(lib_path):
     assert tn.tn_row_words(0) == 0
-    assert tn.tn_row_words(1) == 4
-    assert tn.tn_row_words(256) == 4
-    assert tn.tn_row_words(257) == 8
-    assert tn.tn_row_words(100_000) == 1564
+    assert tn.tn_row_words(1) == 16
+    assert tn.tn_row_words(1024) == 16
+    assert tn.tn_row_words(1025) == 32
+    assert tn.tn_row_words(100_000) == 1568
     assert tn.tn_status_string(tn.TN_ERANGE).startswith("TN_ERANGE")
     assert tn.tn_status_string(12345) == "unknown tn_status"
 
