@@ -114,7 +114,7 @@ def test_schedule_options_identical(slab, window):
     assert np.array_equal(host_matrix(S, n), oracle.component_matrix(u, v, t, n))
 
 
-@pytest.mark.parametrize("smem_rows", [1, 0, 2000])
+@pytest.mark.parametrize("smem_rows", [1, 0, 1000])
 def test_local_and_global_windows_identical(smem_rows):
     """smem_rows=1 sends every window through the global-memory path; the
     default and a large buffer apply most windows in shared memory."""
@@ -127,6 +127,24 @@ def test_local_and_global_windows_identical(smem_rows):
         assert st["local_windows"] == 0
     else:
         assert st["local_windows"] > 0
+    S = torch.empty((n, tn.tn_row_words(n)), dtype=torch.int64, device="cuda")
+    plan.apply(S, init=True)
+    assert plan.status() == 0
+    assert np.array_equal(host_matrix(S, n), oracle.component_matrix(u, v, t, n))
+
+
+def test_carry_across_empty_window():
+    """A tie group that spans a nominal window boundary leaves an empty window
+    between two local records that share rows."""
+    rng = np.random.default_rng(15)
+    n = 40
+    t = np.concatenate([np.arange(60), np.full(70, 60), 61 + np.arange(200)]).astype(np.int64)
+    u = rng.integers(0, n, len(t)).astype(np.uint32)
+    v = rng.integers(0, n, len(t)).astype(np.uint32)
+    du, dv, dt = dev_events(u, v, t)
+    plan = tn.Plan(du, dv, dt, n, window_events=64, slab_words=16)
+    st = plan.stats()
+    assert st["local_windows"] >= 2 and st["items"] < st["windows"]  # some window is empty
     S = torch.empty((n, tn.tn_row_words(n)), dtype=torch.int64, device="cuda")
     plan.apply(S, init=True)
     assert plan.status() == 0
