@@ -72,6 +72,7 @@ typedef int32_t tn_status;
 #define TN_ENOMEM (-4)   /* device scratch allocation failed */
 #define TN_ECUDA (-5)    /* a CUDA runtime call failed */
 #define TN_ETIMEOUT (-6) /* a bounded device-side wait expired */
+#define TN_ESCRATCH (-7) /* the problem needs more than the fixed scratch of a no-alloc entry point */
 
 /* Flags of tn_component_matrix / tn_component_columns / tn_plan_apply. */
 #define TN_INIT_IDENTITY 1u /* initialise S first: identity, or the source columns */
@@ -264,6 +265,35 @@ tn_status tn_hash_proxy(const uint32_t *u, const uint32_t *v, uint64_t m, uint32
 tn_status tn_hash_estimate(const uint64_t *P, uint32_t R, uint32_t k, const uint32_t *H,
                            uint32_t n, const uint32_t *src, uint32_t nsrc, uint32_t *est,
                            void *stream);
+
+/* ---------------------------------------------------------------------------
+ * tn_hash_estimate_noalloc -- the same fusion as tn_hash_estimate (same
+ * arguments, same result bit for bit) for callers that must not allocate.
+ * The paper has no counterpart to this entry point: it only changes where the
+ * scratch lives.
+ *
+ * It allocates nothing: no cudaMalloc / cudaFree / stream-ordered allocator or
+ * allocating library call.  Its scratch is one fixed device array of
+ * TN_NOALLOC_SCRATCH_BYTES bytes per device, owned by the library (static
+ * storage of the library's module), whose address is looked up once per
+ * device on the first call:
+ *   - a 4-byte flag for the source-id check, cleared on the stream before
+ *     every validating call;
+ *   - the per-CTA fusion tables when R * k exceeds the 200 KiB shared-memory
+ *     table: R * k * ceil(nsrc / 8) bytes, at most TN_NOALLOC_TABLE_BYTES.
+ *     A problem that needs more returns TN_ESCRATCH before anything is
+ *     enqueued (use tn_hash_estimate, which allocates, or fewer sources).
+ * The scratch is shared by every call on a device: calls that overlap in time
+ * (other streams, other threads) race on it, so serialise them.  The first
+ * call on a device resolves the scratch address and must come before any
+ * stream capture; nothing is claimed about capturing this call in a graph.
+ * Asynchronous when src is NULL; validating with src (ids >= n: TN_ERANGE).
+ */
+#define TN_NOALLOC_TABLE_BYTES (8u << 20)
+#define TN_NOALLOC_SCRATCH_BYTES (TN_NOALLOC_TABLE_BYTES + 256u)
+tn_status tn_hash_estimate_noalloc(const uint64_t *P, uint32_t R, uint32_t k, const uint32_t *H,
+                                   uint32_t n, const uint32_t *src, uint32_t nsrc, uint32_t *est,
+                                   void *stream);
 
 /* ---------------------------------------------------------------------------
  * tn_out_component_sizes_host -- the whole exact path from HOST arrays:

@@ -21,13 +21,14 @@ import os
 __all__ = [
     "TnError", "load_library", "tn_row_words", "tn_status_string", "tn_kernel_launches", "tn_init_matrix",
     "tn_component_matrix", "tn_component_columns", "tn_out_sizes",
-    "tn_hash_proxy", "tn_hash_estimate", "tn_out_component_sizes_host",
+    "tn_hash_proxy", "tn_hash_estimate", "tn_hash_estimate_noalloc", "tn_out_component_sizes_host",
     "Plan", "tn_plan_apply_batch",
-    "TN_OK", "TN_EINVAL", "TN_ERANGE", "TN_EORDER", "TN_ENOMEM", "TN_ECUDA", "TN_ETIMEOUT",
+    "TN_OK", "TN_EINVAL", "TN_ERANGE", "TN_EORDER", "TN_ENOMEM", "TN_ECUDA", "TN_ETIMEOUT", "TN_ESCRATCH",
     "TN_INIT_IDENTITY",
 ]
 
 TN_OK, TN_EINVAL, TN_ERANGE, TN_EORDER, TN_ENOMEM, TN_ECUDA, TN_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
+TN_ESCRATCH = -7
 TN_INIT_IDENTITY = 1
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -88,6 +89,7 @@ def load_library(path: str | None = None):
         "tn_plan_destroy": ([vp, vp], i32),
         "tn_hash_proxy": ([vp, vp, u64, u32, u32, u32, u64, vp, vp, vp, vp], i32),
         "tn_hash_estimate": ([vp, u32, u32, vp, u32, vp, u32, vp, vp], i32),
+        "tn_hash_estimate_noalloc": ([vp, u32, u32, vp, u32, vp, u32, vp, vp], i32),
         "tn_out_component_sizes_host": ([vp, vp, vp, u64, u32, vp, vp, vp], i32),
     }
     for name, (args, res) in sigs.items():
@@ -240,6 +242,23 @@ def tn_hash_estimate(P, R: int, k: int, H, n: int, src=None, stream=None):
     est = torch.empty(nsrc, dtype=torch.int32, device=P.device)
     _check(lib.tn_hash_estimate(_ptr(P), R, k, _ptr(H), n, _ptr(src), nsrc, _ptr(est), _stream(stream)),
            "tn_hash_estimate")
+    return est
+
+
+def tn_hash_estimate_noalloc(P, R: int, k: int, H, n: int, est, src=None, stream=None):
+    """Fusion by intersection into the caller's est int32[nsrc]; the library
+    allocates nothing (its scratch is one fixed device array per device)."""
+    lib = load_library()
+    _dev(P, ("int64", "uint64"), "P")
+    _dev(H, ("int32", "uint32"), "H")
+    _dev(est, ("int32", "uint32"), "est")
+    nsrc = n if src is None else src.numel()
+    if src is not None:
+        _dev(src, ("int32", "uint32"), "src")
+    if est.numel() < nsrc:
+        raise ValueError("est is smaller than the number of sources")
+    _check(lib.tn_hash_estimate_noalloc(_ptr(P), R, k, _ptr(H), n, _ptr(src), nsrc, _ptr(est), _stream(stream)),
+           "tn_hash_estimate_noalloc")
     return est
 
 

@@ -43,6 +43,7 @@ extern "C" const char *tn_status_string(tn_status s)
     case TN_ENOMEM: return "TN_ENOMEM: device allocation failed";
     case TN_ECUDA: return "TN_ECUDA: CUDA runtime error";
     case TN_ETIMEOUT: return "TN_ETIMEOUT: bounded device wait expired";
+    case TN_ESCRATCH: return "TN_ESCRATCH: problem larger than the fixed scratch of a no-alloc entry point";
     default: return "unknown tn_status";
     }
 }

@@ -231,3 +231,81 @@ extern "C" tn_status tn_hash_estimate(const uint64_t *P, uint32_t R, uint32_t k,
     if (gtable) TN_CUDA_TRY(cudaFreeAsync(gtable, st));
     return TN_OK;
 }
+
+// ---------------- fusion without allocation ----------------
+// Same kernels as tn_hash_estimate; the source-check flag and the per-CTA
+// tables of the global-table path live in one fixed device array of this
+// module instead of the stream-ordered allocator.  Bytes [0, 4) hold the
+// flag, the tables start at byte 256.
+#include <mutex>
+
+namespace tn {
+static __device__ __align__(256) uint8_t g_noalloc_scratch[TN_NOALLOC_SCRATCH_BYTES];
+constexpr uint64_t kNoallocTableOffset = 256;
+constexpr int kNoallocMaxDevices = 64;
+
+// Address of the scratch on the current device, looked up once per device.
+static tn_status noalloc_scratch(uint8_t **out)
+{
+    static std::mutex mu;
+    static uint8_t *addr[kNoallocMaxDevices] = {nullptr};
+    int dev = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) {
+        tn_internal_set_cuda_error(err);
+        return TN_ECUDA;
+    }
+    if (dev < 0 || dev >= kNoallocMaxDevices) return TN_EINVAL;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        err = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (err != cudaSuccess) {
+            tn_internal_set_cuda_error(err);
+            return TN_ECUDA;
+        }
+        addr[dev] = (uint8_t *)p;
+    }
+    *out = addr[dev];
+    return TN_OK;
+}
+}  // namespace tn
+
+extern "C" tn_status tn_hash_estimate_noalloc(const uint64_t *P, uint32_t R, uint32_t k, const uint32_t *H,
+                                              uint32_t n, const uint32_t *src, uint32_t nsrc, uint32_t *est,
+                                              void *stream)
+{
+    if (!P || !H || !est || R == 0 || R > 64 || k == 0 || n == 0 || nsrc == 0) return TN_EINVAL;
+    if (!src && nsrc != n) return TN_EINVAL;
+    const uint64_t ldk = tn_row_words(k);
+    const uint64_t table_bytes = (uint64_t)R * k;
+    const unsigned batches = (nsrc + kEstSources - 1) / kEstSources;
+    const bool smem_table = table_bytes <= 200 * 1024;
+    if (!smem_table && table_bytes * batches > TN_NOALLOC_TABLE_BYTES) return TN_ESCRATCH;
+    uint8_t *scratch = nullptr;
+    const tn_status s = noalloc_scratch(&scratch);
+    if (s != TN_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (src) {  // validating: source ids must be node ids
+        int32_t *dbad = reinterpret_cast<int32_t *>(scratch), hbad = 0;
+        TN_CUDA_TRY(cudaMemsetAsync(dbad, 0, sizeof(int32_t), st));
+        tn_internal_count_launches(1);
+        check_sources_kernel<<<(nsrc + 255) / 256 < 1024 ? (nsrc + 255) / 256 : 1024, 256, 0, st>>>(src, nsrc, n, dbad);
+        TN_CUDA_TRY(cudaMemcpyAsync(&hbad, dbad, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        TN_CUDA_TRY(cudaStreamSynchronize(st));
+        if (hbad) return TN_ERANGE;
+    }
+    TN_CUDA_TRY(cudaMemsetAsync(est, 0, (size_t)nsrc * sizeof(uint32_t), st));
+    size_t smem = 0;
+    uint8_t *gtable = nullptr;
+    if (smem_table) {
+        smem = table_bytes;
+        TN_CUDA_TRY(cudaFuncSetAttribute(estimate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    } else {
+        gtable = scratch + kNoallocTableOffset;  // every byte is written by its CTA before it is read
+    }
+    tn_internal_count_launches(1);
+    estimate_kernel<<<dim3(batches, 1), kEstThreads, smem, st>>>(P, R, k, ldk, H, n, src, nsrc, est, gtable);
+    TN_CUDA_TRY(cudaGetLastError());
+    return TN_OK;
+}
