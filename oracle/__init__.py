@@ -18,6 +18,8 @@ arrays.  Functions cite the paper passage they follow:
   DefInvHComp, DefEstOCMerge).
 * ``emd_w1``            -- Earth-Mover (Wasserstein-1) distance between two
   equal-size samples of sizes (Section 4.4).
+* ``error_stats``       -- absolute, relative and W1 error of estimates against
+  exact sizes (Section 4.4).
 """
 from __future__ import annotations
 
@@ -87,6 +89,10 @@ def _load():
         lib.tnref_hash_estimate.argtypes = [_u64p, ctypes.c_uint32, ctypes.c_uint32, _u32p,
                                             ctypes.c_uint32, ctypes.c_void_p, ctypes.c_uint64, _u32p]
         lib.tnref_hash_estimate.restype = ctypes.c_int
+        _u64o = ctypes.POINTER(ctypes.c_uint64)
+        _f64o = ctypes.POINTER(ctypes.c_double)
+        lib.tnref_error_stats.argtypes = [_u32p, _u32p, ctypes.c_uint64, _u64o, _u64o, _u64o, _f64o, _f64o]
+        lib.tnref_error_stats.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -240,3 +246,22 @@ def emd_w1(a, b) -> float:
     if a.shape != b.shape:
         raise ValueError("emd_w1 expects equal-size samples")
     return float(np.abs(a - b).mean()) if a.size else 0.0
+
+
+def error_stats(est, exact) -> dict:
+    """Error of estimated against exact out-component sizes over the same
+    sources (Section 4.4): sum / max absolute error, mean / max relative error
+    (relative to the exact size) and the Wasserstein-1 distance between the two
+    size distributions (``w1_num`` = count * W1, an integer)."""
+    a = np.ascontiguousarray(est, dtype=np.uint32)
+    b = np.ascontiguousarray(exact, dtype=np.uint32)
+    if a.shape != b.shape:
+        raise ValueError("error_stats expects equal-size samples")
+    sa, ma, wn = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    rs, mr = ctypes.c_double(), ctypes.c_double()
+    _check(_load().tnref_error_stats(a, b, len(a), ctypes.byref(sa), ctypes.byref(ma), ctypes.byref(wn),
+                                     ctypes.byref(rs), ctypes.byref(mr)))
+    c = len(a)
+    return dict(count=c, sum_abs=sa.value, max_abs=ma.value, w1_num=wn.value, rel_sum=rs.value,
+                max_rel=mr.value, mean_abs=sa.value / c if c else 0.0, mean_rel=rs.value / c if c else 0.0,
+                w1=wn.value / c if c else 0.0)

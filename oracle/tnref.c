@@ -360,3 +360,63 @@ int tnref_hash_estimate(const uint64_t *P, uint32_t R, uint32_t k,
     }
     return TNREF_OK;
 }
+
+/* ---------------------------------------------------------------------------
+ * Error of the hashed estimate against the exact sizes (Section 4.4 compares
+ * the estimated and the exact out-component size distributions with the
+ * Earth-Mover distance).  For two samples a (estimates) and b (exact sizes) of
+ * the same sources, count entries each:
+ *   sum_abs = sum |a_s - b_s|,        max_abs = max |a_s - b_s|,
+ *   rel_sum = sum |a_s - b_s| / b_s,  max_rel = max |a_s - b_s| / b_s
+ *   (in double, summed in source order; b_s >= 1 since a node reaches itself),
+ *   w1_num  = sum_i |sort(a)_i - sort(b)_i|, i.e. count * W1 between the two
+ *   empirical distributions (for equal-size samples the optimal transport
+ *   plan matches the sorted orders).
+ * Returns TNREF_EINVAL if an exact size is 0.
+ * ------------------------------------------------------------------------- */
+static int cmp_u32(const void *x, const void *y)
+{
+    uint32_t a = *(const uint32_t *)x, b = *(const uint32_t *)y;
+    return (a > b) - (a < b);
+}
+
+int tnref_error_stats(const uint32_t *a, const uint32_t *b, uint64_t count,
+                      uint64_t *sum_abs, uint64_t *max_abs, uint64_t *w1_num,
+                      double *rel_sum, double *max_rel)
+{
+    uint64_t s = 0, mx = 0, w = 0;
+    double rs = 0.0, mr = 0.0;
+    for (uint64_t i = 0; i < count; ++i) {
+        if (b[i] == 0)
+            return TNREF_EINVAL;
+        uint64_t d = a[i] > b[i] ? (uint64_t)(a[i] - b[i]) : (uint64_t)(b[i] - a[i]);
+        s += d;
+        if (d > mx)
+            mx = d;
+        double r = (double)d / (double)b[i];
+        rs += r;
+        if (r > mr)
+            mr = r;
+    }
+    uint32_t *sa = malloc(count * sizeof(uint32_t) + 1);
+    uint32_t *sb = malloc(count * sizeof(uint32_t) + 1);
+    if (!sa || !sb) {
+        free(sa);
+        free(sb);
+        return TNREF_ENOMEM;
+    }
+    memcpy(sa, a, count * sizeof(uint32_t));
+    memcpy(sb, b, count * sizeof(uint32_t));
+    qsort(sa, count, sizeof(uint32_t), cmp_u32);
+    qsort(sb, count, sizeof(uint32_t), cmp_u32);
+    for (uint64_t i = 0; i < count; ++i)
+        w += sa[i] > sb[i] ? (uint64_t)(sa[i] - sb[i]) : (uint64_t)(sb[i] - sa[i]);
+    free(sa);
+    free(sb);
+    *sum_abs = s;
+    *max_abs = mx;
+    *w1_num = w;
+    *rel_sum = rs;
+    *max_rel = mr;
+    return TNREF_OK;
+}

@@ -375,3 +375,45 @@ def test_emd_matches_scipy():
     b = rng.integers(1, 700, 1000)
     assert oracle.emd_w1(a, b) == pytest.approx(stats.wasserstein_distance(a, b), rel=1e-12)
     assert oracle.emd_w1(a, a) == 0.0
+
+
+def test_error_stats_hand_example():
+    # est = (3, 1, 4), exact = (1, 1, 2): |d| = (2, 0, 2), d/exact = (2, 0, 1)
+    # sorted: (1, 3, 4) vs (1, 1, 2) -> W1 * 3 = 0 + 2 + 2
+    st = oracle.error_stats([3, 1, 4], [1, 1, 2])
+    assert (st["sum_abs"], st["max_abs"], st["w1_num"]) == (4, 2, 4)
+    assert st["rel_sum"] == 3.0 and st["max_rel"] == 2.0
+    assert st["mean_abs"] == pytest.approx(4 / 3) and st["w1"] == pytest.approx(4 / 3)
+
+
+def test_error_stats_closed_forms():
+    rng = np.random.default_rng(3)
+    b = rng.integers(1, 10_000, 5000).astype(np.uint32)
+    # a constant shift moves the whole distribution: W1 = shift = mean |d|
+    st = oracle.error_stats(b + 7, b)
+    assert st["w1_num"] == 7 * 5000 and st["sum_abs"] == 7 * 5000 and st["max_abs"] == 7
+    assert st["max_rel"] == pytest.approx(7.0 / b.min(), rel=1e-15)
+    # a permutation keeps the distribution: W1 = 0 while the per-source error is not
+    p = rng.permutation(b)
+    st = oracle.error_stats(p, b)
+    assert st["w1_num"] == 0 and st["sum_abs"] == int(np.abs(p.astype(np.int64) - b).sum()) > 0
+    # identical samples: no error at all
+    st = oracle.error_stats(b, b)
+    assert st["sum_abs"] == st["w1_num"] == st["max_abs"] == 0 and st["rel_sum"] == 0.0
+
+
+def test_error_stats_w1_is_emd():
+    from scipy import stats
+    rng = np.random.default_rng(5)
+    a = rng.integers(1, 900, 3000).astype(np.uint32)
+    b = rng.integers(1, 400, 3000).astype(np.uint32)
+    st = oracle.error_stats(a, b)
+    assert st["w1"] == pytest.approx(stats.wasserstein_distance(a, b), rel=1e-12)
+    assert st["w1"] == pytest.approx(oracle.emd_w1(a, b), rel=1e-12)
+    # W1 never exceeds the mean per-source error (the identity matching is a transport plan)
+    assert st["w1_num"] <= st["sum_abs"]
+
+
+def test_error_stats_rejects_zero_exact_size():
+    with pytest.raises(Exception):
+        oracle.error_stats([1, 2], [1, 0])
