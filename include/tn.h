@@ -267,6 +267,34 @@ tn_status tn_hash_estimate(const uint64_t *P, uint32_t R, uint32_t k, const uint
                            void *stream);
 
 /* ---------------------------------------------------------------------------
+ * tn_error_stats -- error of estimated against exact out-component sizes of
+ * the same sources (Section 4.4 reports the Earth-Mover distance between the
+ * estimated and the exact size distributions).
+ *
+ *   est, exact  uint32[count] (device): est[s] and exact[s] belong to the same
+ *               source; every exact size is >= 1 (a node reaches itself).
+ *   max_value   bound on every value (e.g. n); sizes the histograms.
+ *   out         HOST pointer, filled on success:
+ *     sum_abs  = sum |est - exact|          max_abs = max |est - exact|
+ *     w1_num   = count * W1, W1 the Wasserstein-1 distance between the two
+ *                empirical distributions = sum over integers x of
+ *                |#{est <= x} - #{exact <= x}| / count (exact integers)
+ *     rel_sum  = sum |est - exact| / exact  max_rel = max of the same (double;
+ *                rel_sum is summed in an unspecified order)
+ *     mean_abs = sum_abs / count, mean_rel = rel_sum / count, w1 = w1_num / count.
+ * Synchronous (waits for `stream`).  TN_ERANGE if a value exceeds max_value or
+ * an exact size is 0.  Scratch: 8 * (max_value + 1) bytes from the
+ * stream-ordered allocator.
+ */
+typedef struct tn_error_stats {
+    uint64_t count, sum_abs, max_abs, w1_num;
+    double rel_sum, max_rel, mean_abs, mean_rel, w1;
+} tn_error_stats;
+
+tn_status tn_error_stats_compute(const uint32_t *est, const uint32_t *exact, uint32_t count,
+                                 uint32_t max_value, tn_error_stats *out, void *stream);
+
+/* ---------------------------------------------------------------------------
  * tn_hash_estimate_noalloc -- the same fusion as tn_hash_estimate (same
  * arguments, same result bit for bit) for callers that must not allocate.
  * The paper has no counterpart to this entry point: it only changes where the

@@ -21,7 +21,8 @@ import os
 __all__ = [
     "TnError", "load_library", "tn_row_words", "tn_status_string", "tn_kernel_launches", "tn_init_matrix",
     "tn_component_matrix", "tn_component_columns", "tn_out_sizes",
-    "tn_hash_proxy", "tn_hash_estimate", "tn_hash_estimate_noalloc", "tn_out_component_sizes_host",
+    "tn_hash_proxy", "tn_hash_estimate", "tn_hash_estimate_noalloc", "tn_error_stats",
+    "tn_out_component_sizes_host",
     "Plan", "tn_plan_apply_batch",
     "TN_OK", "TN_EINVAL", "TN_ERANGE", "TN_EORDER", "TN_ENOMEM", "TN_ECUDA", "TN_ETIMEOUT", "TN_ESCRATCH",
     "TN_INIT_IDENTITY",
@@ -52,6 +53,12 @@ class TnError(RuntimeError):
 class _Options(ctypes.Structure):
     _fields_ = [("window_events", ctypes.c_uint32), ("slab_words", ctypes.c_uint32),
                 ("smem_rows", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 5)]
+
+
+class _ErrorStats(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_uint64), ("sum_abs", ctypes.c_uint64), ("max_abs", ctypes.c_uint64),
+                ("w1_num", ctypes.c_uint64), ("rel_sum", ctypes.c_double), ("max_rel", ctypes.c_double),
+                ("mean_abs", ctypes.c_double), ("mean_rel", ctypes.c_double), ("w1", ctypes.c_double)]
 
 
 class _Stats(ctypes.Structure):
@@ -90,6 +97,7 @@ def load_library(path: str | None = None):
         "tn_hash_proxy": ([vp, vp, u64, u32, u32, u32, u64, vp, vp, vp, vp], i32),
         "tn_hash_estimate": ([vp, u32, u32, vp, u32, vp, u32, vp, vp], i32),
         "tn_hash_estimate_noalloc": ([vp, u32, u32, vp, u32, vp, u32, vp, vp], i32),
+        "tn_error_stats_compute": ([vp, vp, u32, u32, ctypes.POINTER(_ErrorStats), vp], i32),
         "tn_out_component_sizes_host": ([vp, vp, vp, u64, u32, vp, vp, vp], i32),
     }
     for name, (args, res) in sigs.items():
@@ -260,6 +268,20 @@ def tn_hash_estimate_noalloc(P, R: int, k: int, H, n: int, est, src=None, stream
     _check(lib.tn_hash_estimate_noalloc(_ptr(P), R, k, _ptr(H), n, _ptr(src), nsrc, _ptr(est), _stream(stream)),
            "tn_hash_estimate_noalloc")
     return est
+
+
+def tn_error_stats(est, exact, max_value: int, stream=None) -> dict:
+    """Error of estimated against exact sizes of the same sources (Section 4.4):
+    absolute, relative and Wasserstein-1 (``w1_num`` = count * W1, exact)."""
+    lib = load_library()
+    _dev(est, ("int32", "uint32"), "est")
+    _dev(exact, ("int32", "uint32"), "exact")
+    if est.numel() != exact.numel():
+        raise ValueError("est and exact must have the same length")
+    out = _ErrorStats()
+    _check(lib.tn_error_stats_compute(_ptr(est), _ptr(exact), est.numel(), max_value, ctypes.byref(out),
+                                      _stream(stream)), "tn_error_stats")
+    return {name: getattr(out, name) for name, _ in _ErrorStats._fields_}
 
 
 def tn_out_component_sizes_host(u, v, t, n: int):

@@ -350,3 +350,64 @@ def test_estimate_global_table_path():
     assert np.array_equal(u32(est), oracle.hash_estimate(Pref, Href, n, ref_src))
     pu0, pv0 = oracle.proxy_events(u, v, Href[0])
     assert np.array_equal(Pref[0], oracle.component_matrix(pu0, pv0, t, k))
+
+
+# --------------------------------------------------------------------------
+# error of the estimate (Section 4.4)
+# --------------------------------------------------------------------------
+def _err_check(est, exact, maxv):
+    g = tn.tn_error_stats(torch.from_numpy(est.view(np.int32)).cuda(),
+                          torch.from_numpy(exact.view(np.int32)).cuda(), maxv)
+    want = oracle.error_stats(est, exact)
+    for key in ("count", "sum_abs", "max_abs", "w1_num"):
+        assert g[key] == want[key], key
+    assert g["max_rel"] == want["max_rel"]  # one correctly rounded division per source
+    # the relative-error sum is a float sum in another order: |error| <= count * eps * sum
+    assert g["rel_sum"] == pytest.approx(want["rel_sum"], rel=max(1e-15, len(est) * 2.3e-16), abs=1e-300)
+    return g
+
+
+@pytest.mark.parametrize("count,maxv,seed", [(1, 5, 0), (1000, 700, 1), (100_000, 1_000_000, 2), (4097, 3, 3)])
+def test_error_stats_match_oracle(count, maxv, seed):
+    rng = np.random.default_rng(seed)
+    exact = rng.integers(1, maxv + 1, count).astype(np.uint32)
+    est = np.minimum(exact + rng.integers(0, 50, count), maxv).astype(np.uint32)
+    _err_check(est, exact, maxv)
+    _err_check(exact, exact, maxv)
+
+
+def test_error_stats_range_errors():
+    a = torch.tensor([1, 2, 9], dtype=torch.int32, device="cuda")
+    b = torch.tensor([1, 2, 3], dtype=torch.int32, device="cuda")
+    with pytest.raises(tn.TnError) as exc:
+        tn.tn_error_stats(a, b, 8)  # 9 > max_value
+    assert exc.value.status == tn.TN_ERANGE
+    with pytest.raises(tn.TnError) as exc:
+        tn.tn_error_stats(b, torch.tensor([1, 0, 3], dtype=torch.int32, device="cuda"), 8)  # exact size 0
+    assert exc.value.status == tn.TN_ERANGE
+
+
+def test_estimate_error_end_to_end():
+    """Hashed estimates against exact sizes of sampled sources, all on the GPU."""
+    n, m, k, R = 3000, 40_000, 300, 4
+    u, v, t = synth.activity_driven(n, m, seed=21)
+    du, dv, dt = dev_events(u, v, t)
+    H, pu, pv = tn.tn_hash_proxy(du, dv, n, k, R, 9)
+    P = torch.empty((R, k, tn.tn_row_words(k)), dtype=torch.int64, device="cuda")
+    plans = [tn.Plan(pu[j].contiguous(), pv[j].contiguous(), dt, k) for j in range(R)]
+    tn.tn_plan_apply_batch(plans, [P[j] for j in range(R)], init=True)
+    rng = np.random.default_rng(21)
+    src_np = np.sort(rng.choice(n, 256, replace=False)).astype(np.uint32)
+    src = torch.from_numpy(src_np.view(np.int32)).cuda()
+    est = tn.tn_hash_estimate(P, R, k, H, n, src=src)
+    Sx = tn.tn_component_columns(du, dv, dt, n, src)
+    exact, _, _ = tn.tn_out_sizes(Sx, n, len(src_np))
+    g = tn.tn_error_stats(est, exact, n)
+    Href = oracle.hash_nodes(9, R, k, n)
+    want_est = oracle.hash_estimate(oracle.proxy_matrices(u, v, t, Href, k), Href, n, src_np)
+    want_exact = oracle.column_counts(oracle.component_matrix(u, v, t, n, src_np), len(src_np))
+    assert np.array_equal(u32(est), want_est) and np.array_equal(u32(exact), want_exact)
+    want = oracle.error_stats(want_est, want_exact)
+    for key in ("sum_abs", "max_abs", "w1_num"):
+        assert g[key] == want[key]
+    assert (want_est >= want_exact).all()
