@@ -38,6 +38,8 @@ WORKLOADS = {
                      kind="activity", n=100_000, m=10_000_000, seed=2),
     "uniform-small": dict(desc="uniform pairs n=1000 m=20000, t uniform in [0,1e4)", kind="uniform",
                           n=1000, m=20_000, seed=1, t_range=10_000),
+    "serving": dict(desc="serving: Poisson arrivals 200 req/s, n log-uniform [1e3,1e5], m log-uniform [1e4,1e7], "
+                         "uniform endpoints, 4 incremental batches per job", kind="serving", n=0, m=0, seed=5),
 }
 
 
@@ -53,6 +55,9 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--jobs", type=int, default=200, help="serving: number of jobs")
+    ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
+    ap.add_argument("--max-active", type=int, default=16, help="serving: jobs resident at once")
     return ap.parse_args()
 
 
@@ -170,8 +175,41 @@ def cpu_oracle_sample(u, v, t, n, target_s):
     return ms, dt
 
 
+def run_reference_serving(args, w, world):
+    """The oracle on whole jobs of the serving stream, in arrival order, until
+    about --cpu-seconds of CPU time: events/s of the sample."""
+    import oracle
+    from paper_2307_04890_gb300 import synth
+    oracle.build_oracle()
+    specs = synth.serving_jobs(args.jobs, rate=args.rate, seed=w["seed"])
+    done_events, spent, jobs_done = 0, 0.0, 0
+    for spec in specs:
+        if spent >= args.cpu_seconds:
+            break
+        if spec["n"] * spec["m"] > 2e11:  # one job alone would exceed the sample budget
+            continue
+        u, v, t = synth.job_events(spec)
+        t0 = time.perf_counter()
+        oracle.column_counts(oracle.component_matrix(u, v, t, spec["n"]), spec["n"])
+        spent += time.perf_counter() - t0
+        done_events += len(u)
+        jobs_done += 1
+    value = done_events / max(spent, 1e-9)
+    sample = f"{jobs_done} whole jobs of the stream (n*m <= 2e11), one thread, {spent:.1f} s"
+    line = {"impl": "reference", "metric": METRIC + " (serving)", "value": value, "unit": "events/s",
+            "n_gpus": world, "steps": jobs_done, "warmup": 0, "ms_per_step": spent * 1e3 / max(jobs_done, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": w["desc"], "jobs": jobs_done},
+            "cpu_baseline": {"value": value, "unit": "events/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args, w, rank, world):
     if rank != 0:
+        return
+    if w["kind"] == "serving":
+        run_reference_serving(args, w, world)
         return
     u, v, t = make_events(w)
     n = w["n"]
@@ -194,12 +232,81 @@ def run_reference(args, w, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_serving(args, w, rank, world, local_rank):
+    """Continuous admission of a Poisson stream of jobs through tn_server_*.
+    Latency = submit -> out-sizes on the host; throughput = all events (and
+    n * m bit-updates) of all jobs / wall time from the first submit to the
+    last result."""
+    import torch
+    import paper_2307_04890_gb300 as tn
+    from paper_2307_04890_gb300 import synth
+    from paper_2307_04890_gb300.build import build_library
+
+    build_library()
+    tn.load_library()
+    torch.cuda.set_device(local_rank)
+    specs = synth.serving_jobs(args.jobs, rate=args.rate, seed=w["seed"] + 1000 * rank)
+    jobs = []
+    for spec in specs:
+        u, v, t = synth.job_events(spec)
+        offs = np.array([0] + [b for _, b in synth.split_batches(t, 4)], dtype=np.uint64)
+        jobs.append((spec, u, v, t, offs))
+    # warm-up: the first jobs once, unmeasured
+    with tn.Server(max_active=args.max_active) as srv:
+        for spec, u, v, t, offs in jobs[: max(3, args.warmup)]:
+            srv.submit(spec["job"], spec["n"], u, v, t, offs)
+        got = 0
+        while got < min(len(jobs), max(3, args.warmup)):
+            got += len(srv.poll(wait_ms=100))
+    srv = tn.Server(max_active=args.max_active)
+    recs = []
+    with ClockSampler(torch.cuda.current_device()) as clocks:
+        t0 = time.perf_counter()
+        for spec, u, v, t, offs in jobs:
+            delay = t0 + spec["arrival"] - time.perf_counter()
+            if delay > 0:
+                recs += srv.poll(wait_ms=0)
+                time.sleep(max(0.0, t0 + spec["arrival"] - time.perf_counter()))
+            srv.submit(spec["job"], spec["n"], u, v, t, offs)
+        while len(recs) < len(jobs):
+            recs += srv.poll(wait_ms=100)
+        wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    bad = [r for r in recs if r["status"] != 0]
+    lat = np.array([(r["t_done_ns"] - r["t_submit_ns"]) / 1e6 for r in recs])
+    queue = np.array([(r["t_admit_ns"] - r["t_submit_ns"]) / 1e6 for r in sorted(recs, key=lambda r: r["t_submit_ns"])])
+    q = max(1, len(queue) // 4)
+    events = sum(len(j[1]) for j in jobs)
+    bit_updates = sum(j[0]["n"] * len(j[1]) for j in jobs)
+    result = {"metric": METRIC + " (serving)", "value": events / wall, "unit": "events/s", "n_gpus": world,
+              "steps": len(jobs), "warmup": max(3, args.warmup), "ms_per_step": wall * 1e3 / len(jobs),
+              "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+              "config": {"workload": w["desc"], "jobs": len(jobs), "rate_per_s": args.rate,
+                         "max_active": args.max_active, "l2": "per-job matrices up to 1.25 GB; jobs overlap"},
+              "bit_updates_per_s": bit_updates / wall,
+              "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                             "mean": float(lat.mean()), "max": float(lat.max())},
+              "queue_delay_ms": {"first_quarter_median": float(np.median(queue[:q])),
+                                 "last_quarter_median": float(np.median(queue[-q:]))},
+              "offered_events_per_s": events / max(specs[-1]["arrival"], 1e-9),
+              "server": st, "failed_jobs": len(bad), "clocks": clocks.summary(),
+              "e2e": {"value": events / wall, "unit": "events/s",
+                      "h2d_bytes_per_step": events * 16 / len(jobs),
+                      "d2h_bytes_per_step": sum(j[0]["n"] * 4 + 4 for j in jobs) / len(jobs)}}
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+
+
 def main():
     args = parse_args()
     w = WORKLOADS[args.workload]
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if w["kind"] == "serving" and args.impl == "ours":
+        run_serving(args, w, rank, world, local_rank)
+        return
     if args.impl == "reference":
         run_reference(args, w, rank, world)
         return

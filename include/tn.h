@@ -324,6 +324,71 @@ tn_status tn_hash_estimate_noalloc(const uint64_t *P, uint32_t R, uint32_t k, co
                                    void *stream);
 
 /* ---------------------------------------------------------------------------
+ * Serving (Section 3.5: the method is a one-pass streaming algorithm, so a
+ * job's matrix can stay on the device while its event batches arrive).
+ *
+ * A server runs a worker thread on the device that is current when it is
+ * created.  tn_server_submit queues a job; the worker admits queued jobs in
+ * arrival order whenever fewer than max_active jobs are resident and the
+ * job's device memory (matrix + schedules, estimated at submit) fits in
+ * memory_budget, so jobs that arrive while others run join the device as soon
+ * as a slot and memory free up.  Each admitted job runs on its own stream:
+ * its batches are copied in, scheduled and applied in order to one matrix kept
+ * on the device (S <- I first; each batch must start after the previous
+ * one's last timestamp, checked on the device), then its out-sizes (and
+ * largest out-component) are copied to the caller's host buffers.  Jobs on
+ * different streams overlap on the device.  Results are exactly those of
+ * tn_out_component_sizes_host on the concatenated events.
+ */
+typedef struct tn_server tn_server;
+
+typedef struct tn_server_options {
+    uint64_t memory_budget; /* device bytes for resident jobs (0 = 60 % of free memory) */
+    uint32_t max_active;    /* jobs resident at once (0 = 16) */
+    uint32_t window_events; /* plan options of every batch (0 = defaults) */
+    uint32_t slab_words;
+    uint32_t reserved[3];   /* must be zero */
+} tn_server_options;
+
+typedef struct tn_job_record {
+    uint64_t job_id;
+    int32_t status;       /* TN_OK, or the job's error (e.g. TN_EORDER, TN_ERANGE) */
+    uint32_t n;
+    uint64_t events;
+    uint64_t t_submit_ns; /* host steady-clock times: submit, admission, results on the host */
+    uint64_t t_admit_ns;
+    uint64_t t_done_ns;
+} tn_job_record;
+
+typedef struct tn_server_stats {
+    uint64_t queued, active, admitted, completed;
+    uint64_t bytes_in_use, budget, peak_active, peak_bytes;
+} tn_server_stats;
+
+tn_status tn_server_create(const tn_server_options *opt, tn_server **server);
+
+/* Queues job `job_id`: n nodes; HOST arrays u, v, t (pinned or pageable) of
+ * batch_offsets[nbatches] events, batch b = [batch_offsets[b],
+ * batch_offsets[b+1]) (batch_offsets[0] = 0, non-decreasing, each batch
+ * < 2^30 events); out_sizes a HOST uint32[n], argmax a HOST uint32 or NULL.
+ * The caller keeps every buffer alive until the job's record is returned by
+ * tn_server_poll.  TN_ENOMEM if the job could never fit the budget. */
+tn_status tn_server_submit(tn_server *server, uint64_t job_id, uint32_t n, const uint32_t *u,
+                           const uint32_t *v, const int64_t *t, const uint64_t *batch_offsets,
+                           uint32_t nbatches, uint32_t *out_sizes, uint32_t *argmax);
+
+/* Moves up to `capacity` records of finished jobs (in completion order) into
+ * `records`; waits up to wait_ms for the first one.  *count = records moved. */
+tn_status tn_server_poll(tn_server *server, tn_job_record *records, uint32_t capacity,
+                         uint32_t *count, uint32_t wait_ms);
+
+tn_status tn_server_get_stats(tn_server *server, tn_server_stats *stats);
+
+/* Finishes every queued and running job, then stops the worker and frees the
+ * server (records not yet polled are dropped). */
+tn_status tn_server_destroy(tn_server *server);
+
+/* ---------------------------------------------------------------------------
  * tn_out_component_sizes_host -- the whole exact path from HOST arrays:
  * copies u, v, t (host, pinned or pageable) to the device, builds the
  * component matrix from the identity, computes the out-sizes and copies them

@@ -23,7 +23,7 @@ __all__ = [
     "tn_component_matrix", "tn_component_columns", "tn_out_sizes",
     "tn_hash_proxy", "tn_hash_estimate", "tn_hash_estimate_noalloc", "tn_error_stats",
     "tn_out_component_sizes_host",
-    "Plan", "tn_plan_apply_batch",
+    "Plan", "tn_plan_apply_batch", "Server",
     "TN_OK", "TN_EINVAL", "TN_ERANGE", "TN_EORDER", "TN_ENOMEM", "TN_ECUDA", "TN_ETIMEOUT", "TN_ESCRATCH",
     "TN_INIT_IDENTITY",
 ]
@@ -59,6 +59,23 @@ class _ErrorStats(ctypes.Structure):
     _fields_ = [("count", ctypes.c_uint64), ("sum_abs", ctypes.c_uint64), ("max_abs", ctypes.c_uint64),
                 ("w1_num", ctypes.c_uint64), ("rel_sum", ctypes.c_double), ("max_rel", ctypes.c_double),
                 ("mean_abs", ctypes.c_double), ("mean_rel", ctypes.c_double), ("w1", ctypes.c_double)]
+
+
+class _ServerOptions(ctypes.Structure):
+    _fields_ = [("memory_budget", ctypes.c_uint64), ("max_active", ctypes.c_uint32),
+                ("window_events", ctypes.c_uint32), ("slab_words", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 3)]
+
+
+class _JobRecord(ctypes.Structure):
+    _fields_ = [("job_id", ctypes.c_uint64), ("status", ctypes.c_int32), ("n", ctypes.c_uint32),
+                ("events", ctypes.c_uint64), ("t_submit_ns", ctypes.c_uint64), ("t_admit_ns", ctypes.c_uint64),
+                ("t_done_ns", ctypes.c_uint64)]
+
+
+class _ServerStats(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_uint64) for name in ("queued", "active", "admitted", "completed", "bytes_in_use",
+                                                     "budget", "peak_active", "peak_bytes")]
 
 
 class _Stats(ctypes.Structure):
@@ -98,6 +115,11 @@ def load_library(path: str | None = None):
         "tn_hash_estimate": ([vp, u32, u32, vp, u32, vp, u32, vp, vp], i32),
         "tn_hash_estimate_noalloc": ([vp, u32, u32, vp, u32, vp, u32, vp, vp], i32),
         "tn_error_stats_compute": ([vp, vp, u32, u32, ctypes.POINTER(_ErrorStats), vp], i32),
+        "tn_server_create": ([ctypes.POINTER(_ServerOptions), ctypes.POINTER(vp)], i32),
+        "tn_server_submit": ([vp, u64, u32, vp, vp, vp, vp, u32, vp, vp], i32),
+        "tn_server_poll": ([vp, ctypes.POINTER(_JobRecord), u32, ctypes.POINTER(u32), u32], i32),
+        "tn_server_get_stats": ([vp, ctypes.POINTER(_ServerStats)], i32),
+        "tn_server_destroy": ([vp], i32),
         "tn_out_component_sizes_host": ([vp, vp, vp, u64, u32, vp, vp, vp], i32),
     }
     for name, (args, res) in sigs.items():
@@ -368,3 +390,69 @@ def tn_plan_apply_batch(plans, mats, ncols=None, init: bool = True, stream=None)
     _check(lib.tn_plan_apply_batch(hp, hs, hn, count, TN_INIT_IDENTITY if init else 0, _stream(stream)),
            "tn_plan_apply_batch")
     return mats
+
+
+class Server:
+    """Continuous admission of component-matrix jobs (tn_server_*).
+
+    ``submit`` takes host numpy arrays and keeps them (and the result buffer)
+    alive until the job's record comes back from ``poll``; ``results[job_id]``
+    then holds ``(out_sizes, argmax)``.
+    """
+
+    def __init__(self, memory_budget: int = 0, max_active: int = 0, window_events: int = 0, slab_words: int = 0):
+        lib = load_library()
+        opt = _ServerOptions(memory_budget, max_active, window_events, slab_words)
+        h = ctypes.c_void_p()
+        _check(lib.tn_server_create(ctypes.byref(opt), ctypes.byref(h)), "tn_server_create")
+        self._h = h
+        self._keep = {}
+        self.results = {}
+
+    def submit(self, job_id: int, n: int, u, v, t, batch_offsets):
+        import numpy as np
+        lib = load_library()
+        u = np.ascontiguousarray(u, dtype=np.uint32)
+        v = np.ascontiguousarray(v, dtype=np.uint32)
+        t = np.ascontiguousarray(t, dtype=np.int64)
+        offs = np.ascontiguousarray(batch_offsets, dtype=np.uint64)
+        if offs[-1] != len(u) or len(v) != len(u) or len(t) != len(u):
+            raise ValueError("batch offsets must end at the number of events")
+        out = np.zeros(n, dtype=np.uint32)
+        am = np.zeros(1, dtype=np.uint32)
+        self._keep[job_id] = (u, v, t, offs, out, am)
+        _check(lib.tn_server_submit(self._h, job_id, n, u.ctypes.data, v.ctypes.data, t.ctypes.data,
+                                    offs.ctypes.data, len(offs) - 1, out.ctypes.data, am.ctypes.data),
+               "tn_server_submit")
+
+    def poll(self, wait_ms: int = 0, capacity: int = 256):
+        """Records of finished jobs: dicts with job_id, status, n, events and
+        the submit / admit / done host times in ns."""
+        lib = load_library()
+        recs = (_JobRecord * capacity)()
+        cnt = ctypes.c_uint32()
+        _check(lib.tn_server_poll(self._h, recs, capacity, ctypes.byref(cnt), wait_ms), "tn_server_poll")
+        out = []
+        for r in recs[: cnt.value]:
+            d = {name: getattr(r, name) for name, _ in _JobRecord._fields_}
+            kept = self._keep.pop(d["job_id"], None)
+            if kept is not None:
+                self.results[d["job_id"]] = (kept[4], int(kept[5][0]))
+            out.append(d)
+        return out
+
+    def stats(self) -> dict:
+        st = _ServerStats()
+        _check(load_library().tn_server_get_stats(self._h, ctypes.byref(st)), "tn_server_get_stats")
+        return {name: getattr(st, name) for name, _ in _ServerStats._fields_}
+
+    def close(self):
+        if self._h:
+            _check(load_library().tn_server_destroy(self._h), "tn_server_destroy")
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

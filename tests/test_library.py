@@ -58,3 +58,12 @@ def test_binding_fails_loudly_without_library(tmp_path):
     res = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True,
                          cwd=os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     assert res.returncode != 0 and "not found" in res.stderr
+
+
+def test_server_needs_a_device():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(tn.TnError) as exc:
+        tn.Server()
+    assert exc.value.status == tn.TN_ECUDA
