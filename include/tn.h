@@ -230,6 +230,49 @@ tn_status tn_plan_get_stats(const tn_plan *plan, tn_plan_stats *stats);
 tn_status tn_plan_destroy(tn_plan *plan, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * Batched application as a CUDA graph (Section 4.2: the R proxy networks of a
+ * hashed network are independent and are built together).
+ *
+ * tn_graph_capture_batch records one tn_plan_apply_batch of these arguments
+ * (with `flags`) into a CUDA graph on a private stream and instantiates it;
+ * tn_graph_launch replays it on `stream` (one launch), recomputing the same
+ * matrices from the same plans.  The plans and matrices must stay alive and
+ * unchanged in size while the graph exists.  The first plan status error
+ * still gates the replay as it gates a direct call.
+ */
+typedef struct tn_graph tn_graph;
+
+tn_status tn_graph_capture_batch(const tn_plan *const *plans, uint64_t *const *S,
+                                 const uint32_t *ncols, uint32_t count, uint32_t flags,
+                                 tn_graph **graph);
+tn_status tn_graph_launch(tn_graph *graph, void *stream);
+tn_status tn_graph_destroy(tn_graph *graph);
+
+/* ---------------------------------------------------------------------------
+ * tn_autotune -- picks the plan options (slab width = columns per CTA, window
+ * depth, shared-memory row buffer = CTAs per SM) for a batch of `replicas`
+ * networks shaped like (u, v, t, m, n), by timing every candidate on the
+ * first `sample_events` events (0 = all) applied to `replicas` scratch
+ * matrices.  Candidates: slab 2/4/8/16 words (at most the row width), window
+ * 320/640/1024 events, row buffer 160 or 80 KB.  The choice is cached per
+ * (device, n, replicas, floor(log2 m)) for the life of the process.  When the
+ * scratch matrices would exceed 8 GiB nothing is timed and the defaults
+ * (all-zero options) are returned with tried = 0.  Synchronous.
+ */
+typedef struct tn_tune_result {
+    tn_plan_options best;   /* options to pass to tn_plan_create */
+    float best_ms;          /* batched apply time of the sample with them */
+    uint32_t tried;         /* candidates timed (0: defaults, not timed) */
+    uint32_t cached;        /* 1 if the result came from the cache */
+    uint32_t pad;
+    uint64_t sample_events;
+} tn_tune_result;
+
+tn_status tn_autotune(const uint32_t *u, const uint32_t *v, const int64_t *t, uint64_t m,
+                      uint32_t n, uint32_t replicas, uint64_t sample_events, void *stream,
+                      tn_tune_result *result);
+
+/* ---------------------------------------------------------------------------
  * tn_hash_proxy -- network hashing (Section 4.1).
  *
  * Hash family: Thorup-Zhang 2-character tabulation with a derived character.

@@ -23,7 +23,7 @@ __all__ = [
     "tn_component_matrix", "tn_component_columns", "tn_out_sizes",
     "tn_hash_proxy", "tn_hash_estimate", "tn_hash_estimate_noalloc", "tn_error_stats",
     "tn_out_component_sizes_host",
-    "Plan", "tn_plan_apply_batch", "Server",
+    "Plan", "tn_plan_apply_batch", "Server", "BatchGraph", "tn_autotune",
     "TN_OK", "TN_EINVAL", "TN_ERANGE", "TN_EORDER", "TN_ENOMEM", "TN_ECUDA", "TN_ETIMEOUT", "TN_ESCRATCH",
     "TN_INIT_IDENTITY",
 ]
@@ -78,6 +78,11 @@ class _ServerStats(ctypes.Structure):
                                                      "budget", "peak_active", "peak_bytes")]
 
 
+class _TuneResult(ctypes.Structure):
+    _fields_ = [("best", _Options), ("best_ms", ctypes.c_float), ("tried", ctypes.c_uint32),
+                ("cached", ctypes.c_uint32), ("pad", ctypes.c_uint32), ("sample_events", ctypes.c_uint64)]
+
+
 class _Stats(ctypes.Structure):
     _fields_ = [("events", ctypes.c_uint64), ("windows", ctypes.c_uint64), ("levels", ctypes.c_uint64),
                 ("ops", ctypes.c_uint64), ("aux", ctypes.c_uint64), ("temps", ctypes.c_uint64),
@@ -115,6 +120,10 @@ def load_library(path: str | None = None):
         "tn_hash_estimate": ([vp, u32, u32, vp, u32, vp, u32, vp, vp], i32),
         "tn_hash_estimate_noalloc": ([vp, u32, u32, vp, u32, vp, u32, vp, vp], i32),
         "tn_error_stats_compute": ([vp, vp, u32, u32, ctypes.POINTER(_ErrorStats), vp], i32),
+        "tn_graph_capture_batch": ([vp, vp, vp, u32, u32, ctypes.POINTER(vp)], i32),
+        "tn_graph_launch": ([vp, vp], i32),
+        "tn_graph_destroy": ([vp], i32),
+        "tn_autotune": ([vp, vp, vp, u64, u32, u32, u64, vp, ctypes.POINTER(_TuneResult)], i32),
         "tn_server_create": ([ctypes.POINTER(_ServerOptions), ctypes.POINTER(vp)], i32),
         "tn_server_submit": ([vp, u64, u32, vp, vp, vp, vp, u32, vp, vp], i32),
         "tn_server_poll": ([vp, ctypes.POINTER(_JobRecord), u32, ctypes.POINTER(u32), u32], i32),
@@ -337,6 +346,7 @@ class Plan:
         lib = load_library()
         self.m = _events(u, v, t)
         self.n = n
+        self.device = u.device
         opt = _Options(window_events, slab_words, smem_rows)
         h = ctypes.c_void_p()
         if t_after is not None:
@@ -352,7 +362,7 @@ class Plan:
     def apply(self, S, ncols: int | None = None, src=None, t_last=None, init: bool = False, stream=None):
         lib = load_library()
         ncols = self.n if ncols is None else ncols
-        S = _matrix(S, self.n, ncols, S.device if S is not None else None)
+        S = _matrix(S, self.n, ncols, self.device)
         _check(lib.tn_plan_apply(self._h, _ptr(S), ncols, _ptr(src), _ptr(t_last),
                                  TN_INIT_IDENTITY if init else 0, _stream(stream)), "tn_plan_apply")
         return S
@@ -456,3 +466,48 @@ class Server:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def tn_autotune(u, v, t, n: int, replicas: int = 1, sample_events: int = 200_000, stream=None) -> dict:
+    """Plan options for a batch of ``replicas`` networks shaped like (u, v, t, n),
+    chosen by timing the candidates on the first ``sample_events`` events."""
+    lib = load_library()
+    m = _events(u, v, t)
+    res = _TuneResult()
+    _check(lib.tn_autotune(_ptr(u), _ptr(v), _ptr(t), m, n, replicas, sample_events, _stream(stream),
+                           ctypes.byref(res)), "tn_autotune")
+    return {"window_events": res.best.window_events, "slab_words": res.best.slab_words,
+            "smem_rows": res.best.smem_rows, "best_ms": res.best_ms, "tried": res.tried,
+            "cached": bool(res.cached), "sample_events": res.sample_events}
+
+
+class BatchGraph:
+    """One batched application (tn_plan_apply_batch) captured as a CUDA graph;
+    ``launch()`` replays it with a single graph launch."""
+
+    def __init__(self, plans, mats, ncols=None, init: bool = True):
+        lib = load_library()
+        count = len(plans)
+        ncols = ncols or [p.n for p in plans]
+        self._plans, self._mats = list(plans), list(mats)  # keep them alive
+        hp = (ctypes.c_void_p * count)(*[p.handle for p in plans])
+        hs = (ctypes.c_void_p * count)(*[m.data_ptr() for m in mats])
+        hn = (ctypes.c_uint32 * count)(*ncols)
+        h = ctypes.c_void_p()
+        _check(lib.tn_graph_capture_batch(hp, hs, hn, count, TN_INIT_IDENTITY if init else 0, ctypes.byref(h)),
+               "tn_graph_capture_batch")
+        self._h = h
+
+    def launch(self, stream=None):
+        _check(load_library().tn_graph_launch(self._h, _stream(stream)), "tn_graph_launch")
+
+    def destroy(self):
+        if self._h:
+            load_library().tn_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
