@@ -103,6 +103,7 @@ __global__ void proxy_events_kernel(const uint32_t *u, const uint32_t *v, uint64
 // h_j(x_s) in proxy j] = bit h_j(x_s) of row b of P_j.  A node w belongs to
 // the estimate of source s when bit s of AND_j table[j * k + h_j(w)] is set.
 constexpr int kEstSources = 8;
+constexpr uint32_t kBitsliceMinSources = 256;  // from here on the bit-sliced fusion is used
 constexpr int kEstThreads = 256;
 
 __global__ void check_sources_kernel(const uint32_t *src, uint32_t nsrc, uint32_t n, int32_t *bad)
@@ -159,6 +160,108 @@ __global__ void __launch_bounds__(kEstThreads)
     if (threadIdx.x < ns && cnt[threadIdx.x]) atomicAdd(&est[s0 + threadIdx.x], cnt[threadIdx.x]);
 }
 
+// ---------------- fusion, bit-sliced over sources ----------------
+// For many sources the fusion is reorganised around a transposed table:
+//   T[j][b] = bitset over the chunk's sources, bit s = bit h_j(x_s) of row b of P_j
+// (Section 4.2: super-node b reaches h_j(x_s) in proxy j).  Then
+//   est(x_s) = #{w : bit s of AND_j T[j][h_j(w)]},
+// i.e. a column count of the n x nsrc boolean matrix whose row w is the AND
+// of R rows of T -- the same vertical-counter column count as the exact
+// out-sizes.  T rows are padded like component-matrix rows (tn_row_words).
+constexpr int kTabThreads = 256;
+constexpr uint32_t kTabRows = 64;       // proxy rows per CTA
+constexpr uint32_t kTabSources = 8192;  // sources per CTA (their columns cached in shared memory)
+
+__global__ void __launch_bounds__(kTabThreads)
+    bitslice_table_kernel(const uint64_t *P, uint32_t k, uint64_t ldk, const uint32_t *H, uint32_t n,
+                          const uint32_t *src, uint32_t s0, uint32_t ns, uint64_t ldT32, uint32_t *T)
+{
+    __shared__ uint32_t col[kTabSources];
+    const uint32_t j = blockIdx.z;
+    const uint32_t c0 = blockIdx.y * kTabSources;  // first source of this CTA, relative to the chunk
+    const uint32_t cn = min(kTabSources, ns - c0);
+    for (uint32_t q = threadIdx.x; q < cn; q += blockDim.x) {
+        const uint32_t x = src ? src[s0 + c0 + q] : s0 + c0 + q;
+        col[q] = H[(uint64_t)j * n + x];
+    }
+    __syncthreads();
+    const uint32_t b0 = blockIdx.x * kTabRows;
+    const uint32_t b1 = min(k, b0 + kTabRows);
+    // thread t builds 32-bit words (32 sources) of each row
+    const uint32_t words = (cn + 31) / 32;
+    for (uint32_t b = b0; b < b1; ++b) {
+        const uint64_t *row = P + ((uint64_t)j * k + b) * ldk;
+        for (uint32_t wd = threadIdx.x; wd < words; wd += blockDim.x) {
+            uint32_t bits = 0;
+            const uint32_t base = wd * 32;
+#pragma unroll 8
+            for (uint32_t i = 0; i < 32; ++i) {
+                const uint32_t q = base + i;
+                if (q < cn) {
+                    const uint32_t c = col[q];
+                    bits |= (uint32_t)((__ldg(row + (c >> 6)) >> (c & 63)) & 1ull) << i;
+                }
+            }
+            T[((uint64_t)j * k + b) * ldT32 + c0 / 32 + wd] = bits;
+        }
+    }
+}
+
+constexpr int kCountWarps = 8;
+constexpr uint32_t kCountNodes = 4096;  // nodes w per CTA
+
+__global__ void __launch_bounds__(32 * kCountWarps)
+    bitslice_count_kernel(const uint32_t *T, uint64_t ldT32, uint32_t R, uint32_t k, const uint32_t *H, uint32_t n,
+                          uint32_t ns, uint32_t *est)
+{
+    __shared__ uint32_t part[kCountWarps][32][33];
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint64_t word = (uint64_t)blockIdx.x * 32 + lane;  // 32-bit word of a T row (32 sources)
+    const bool live = word < (ns + 31) / 32;                  // words the table kernel wrote
+    const uint32_t w0 = blockIdx.y * kCountNodes;
+    const uint32_t w1 = min(n, w0 + kCountNodes);
+    uint32_t cnt[32];
+#pragma unroll
+    for (int b = 0; b < 32; ++b) cnt[b] = 0;
+    uint32_t c0 = 0, c1 = 0, c2 = 0, c3 = 0, pending = 0;
+    for (uint32_t w = w0 + warp; w < w1; w += kCountWarps) {
+        uint32_t x = live ? 0xFFFFFFFFu : 0u;
+        for (uint32_t j = 0; j < R && x; ++j) {
+            const uint32_t b = __ldg(H + (uint64_t)j * n + w);
+            x &= __ldg(T + ((uint64_t)j * k + b) * ldT32 + word);
+        }
+        // add x to the 4-bit vertical counters
+        const uint32_t carry = c0 & x;
+        c0 ^= x;
+        const uint32_t carry2 = c1 & carry;
+        c1 ^= carry;
+        const uint32_t carry3 = c2 & carry2;
+        c2 ^= carry2;
+        c3 ^= carry3;
+        if (++pending == 15) {
+#pragma unroll
+            for (int b = 0; b < 32; ++b)
+                cnt[b] += ((c0 >> b) & 1u) + (((c1 >> b) & 1u) << 1) + (((c2 >> b) & 1u) << 2) + (((c3 >> b) & 1u) << 3);
+            c0 = c1 = c2 = c3 = 0;
+            pending = 0;
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < 32; ++b)
+        cnt[b] += ((c0 >> b) & 1u) + (((c1 >> b) & 1u) << 1) + (((c2 >> b) & 1u) << 2) + (((c3 >> b) & 1u) << 3);
+#pragma unroll
+    for (int b = 0; b < 32; ++b) part[warp][lane][b] = cnt[b];
+    __syncthreads();
+    for (uint32_t c = threadIdx.x; c < 1024; c += blockDim.x) {
+        const uint32_t l = c >> 5, bit = c & 31u;
+        uint32_t s = 0;
+#pragma unroll
+        for (int w = 0; w < kCountWarps; ++w) s += part[w][l][bit];
+        const uint64_t q = ((uint64_t)blockIdx.x * 32 + l) * 32 + bit;
+        if (s && q < ns) atomicAdd(&est[q], s);
+    }
+}
+
 }  // namespace tn
 
 using namespace tn;
@@ -196,6 +299,30 @@ extern "C" tn_status tn_hash_proxy(const uint32_t *u, const uint32_t *v, uint64_
     return TN_OK;
 }
 
+static tn_status estimate_bitsliced(const uint64_t *P, uint32_t R, uint32_t k, uint64_t ldk, const uint32_t *H,
+                                    uint32_t n, const uint32_t *src, uint32_t nsrc, uint32_t *est, cudaStream_t st)
+{
+    // sources in chunks whose table stays within 2 GiB
+    uint32_t chunk = nsrc < 65536u ? nsrc : 65536u;
+    while (chunk > 1024 && (uint64_t)R * k * tn_row_words(chunk) * 8 > (2ull << 30)) chunk /= 2;
+    const uint64_t ldT32 = 2 * tn_row_words(chunk);
+    uint32_t *T = nullptr;
+    TN_CUDA_TRY(cudaMallocAsync((void **)&T, (uint64_t)R * k * ldT32 * 4, st));
+    for (uint32_t s0 = 0; s0 < nsrc; s0 += chunk) {
+        const uint32_t ns = nsrc - s0 < chunk ? nsrc - s0 : chunk;
+        const uint64_t ld32 = 2 * tn_row_words(ns);
+        // the count kernel reads only the ceil(ns / 32) words the table kernel writes
+        tn_internal_count_launches(2);
+        bitslice_table_kernel<<<dim3((k + kTabRows - 1) / kTabRows, (ns + kTabSources - 1) / kTabSources, R),
+                                kTabThreads, 0, st>>>(P, k, ldk, H, n, src, s0, ns, ld32, T);
+        bitslice_count_kernel<<<dim3((unsigned)((ld32 + 31) / 32), (n + kCountNodes - 1) / kCountNodes),
+                                32 * kCountWarps, 0, st>>>(T, ld32, R, k, H, n, ns, est + s0);
+        TN_CUDA_TRY(cudaGetLastError());
+    }
+    TN_CUDA_TRY(cudaFreeAsync(T, st));
+    return TN_OK;
+}
+
 extern "C" tn_status tn_hash_estimate(const uint64_t *P, uint32_t R, uint32_t k, const uint32_t *H, uint32_t n,
                                       const uint32_t *src, uint32_t nsrc, uint32_t *est, void *stream)
 {
@@ -217,6 +344,7 @@ extern "C" tn_status tn_hash_estimate(const uint64_t *P, uint32_t R, uint32_t k,
     const uint64_t table_bytes = (uint64_t)R * k;
     const unsigned batches = (nsrc + kEstSources - 1) / kEstSources;
     TN_CUDA_TRY(cudaMemsetAsync(est, 0, (size_t)nsrc * sizeof(uint32_t), st));
+    if (nsrc >= kBitsliceMinSources) return estimate_bitsliced(P, R, k, ldk, H, n, src, nsrc, est, st);
     uint8_t *gtable = nullptr;
     size_t smem = 0;
     if (table_bytes <= 200 * 1024) {

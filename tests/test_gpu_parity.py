@@ -411,3 +411,28 @@ def test_estimate_error_end_to_end():
     for key in ("sum_abs", "max_abs", "w1_num"):
         assert g[key] == want[key]
     assert (want_est >= want_exact).all()
+
+
+def test_estimate_bitsliced_chunks_and_both_paths_agree():
+    """All 70,000 sources: the bit-sliced fusion in two source chunks (65,536 +
+    4,464), several table CTAs per replica; sampled sources against the oracle
+    and a few hundred against the byte-table fusion."""
+    n, m, k, R = 70_000, 200_000, 700, 3
+    u, v, t = synth.uniform_events(n, m, t_range=m // 2, seed=41)
+    du, dv, dt = dev_events(u, v, t)
+    H, pu, pv = tn.tn_hash_proxy(du, dv, n, k, R, 17)
+    P = torch.empty((R, k, tn.tn_row_words(k)), dtype=torch.int64, device="cuda")
+    plans = [tn.Plan(pu[j].contiguous(), pv[j].contiguous(), dt, k) for j in range(R)]
+    tn.tn_plan_apply_batch(plans, [P[j] for j in range(R)])
+    est = u32(tn.tn_hash_estimate(P, R, k, H, n))
+    Href = oracle.hash_nodes(17, R, k, n)
+    Pref = oracle.proxy_matrices(u, v, t, Href, k)
+    for j in range(R):
+        assert np.array_equal(host_matrix(P[j], k), Pref[j])
+    rng = np.random.default_rng(41)
+    sample = np.unique(np.concatenate([rng.choice(n, 60, replace=False), [0, 65_535, 65_536, n - 1]])).astype(np.uint32)
+    assert np.array_equal(est[sample], oracle.hash_estimate(Pref, Href, n, sample))
+    few = torch.from_numpy(sample.view(np.int32)).cuda()
+    small = torch.zeros(len(sample), dtype=torch.int32, device="cuda")
+    tn.tn_hash_estimate_noalloc(P, R, k, H, n, small, src=few)  # byte-table fusion
+    assert np.array_equal(u32(small), est[sample])
