@@ -30,7 +30,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "events/s and bit-updates/s (n·m/time) at 1 GB300; achieved HBM GB/s vs peak"
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "stream_kernel_activity_n1e5_m1e7.txt")
+PROFILE_SUMMARIES = {"activity": "stream_kernel_activity_n1e5_m1e7.txt",
+                     "bursty": "stream_kernel_bursty_n5e5_m1e8.txt"}
 KERNEL_SOURCES = ["paper_2307_04890_gb300/csrc/tn_apply.cu", "paper_2307_04890_gb300/csrc/tn_internal.cuh"]
 
 WORKLOADS = {
@@ -38,6 +39,10 @@ WORKLOADS = {
                      kind="activity", n=100_000, m=10_000_000, seed=2),
     "uniform-small": dict(desc="uniform pairs n=1000 m=20000, t uniform in [0,1e4)", kind="uniform",
                           n=1000, m=20_000, seed=1, t_range=10_000),
+    "bursty": dict(desc="power-law bursty n=500000 m=100000000 (degree exponent 2.5, Pareto(1.5, 60 s) gaps, "
+                        "integer seconds: large tie groups)", kind="bursty", n=500_000, m=100_000_000, seed=3),
+    "hashed": dict(desc="hashed estimate n=1000000 m=100000000 activity-driven, k=16384, R=8, 65536 sampled sources",
+                   kind="hashed", n=1_000_000, m=100_000_000, seed=4, k=16384, R=8, nsrc=65536),
     "serving": dict(desc="serving: Poisson arrivals 200 req/s, n log-uniform [1e3,1e5], m log-uniform [1e4,1e7], "
                          "uniform endpoints, 4 incremental batches per job", kind="serving", n=0, m=0, seed=5),
 }
@@ -63,8 +68,10 @@ def parse_args():
 
 def make_events(w, rank=0):
     from paper_2307_04890_gb300 import synth
-    if w["kind"] == "activity":
+    if w["kind"] in ("activity", "hashed"):
         return synth.activity_driven(w["n"], w["m"], seed=w["seed"] + 1000 * rank)
+    if w["kind"] == "bursty":
+        return synth.powerlaw_bursty(w["n"], w["m"], seed=w["seed"] + 1000 * rank)
     return synth.uniform_events(w["n"], w["m"], t_range=w["t_range"], seed=w["seed"] + 1000 * rank)
 
 
@@ -90,7 +97,7 @@ def profiled_traffic(workload_key):
     if it was taken on the current kernel source and this workload."""
     try:
         fields = {}
-        with open(PROFILE_SUMMARY) as f:
+        with open(os.path.join(ROOT, "profiles", PROFILE_SUMMARIES[workload_key])) as f:
             for line in f:
                 if ":" in line and not line.startswith("#"):
                     k, v = line.split(":", 1)
@@ -205,11 +212,44 @@ def run_reference_serving(args, w, world):
     print(json.dumps(line), flush=True)
 
 
+def run_reference_hashed(args, w, world):
+    """The oracle's hashing path on a prefix of the events: hash tables, super-
+    events and the R proxy component matrices (events/s of the prefix)."""
+    import oracle
+    oracle.build_oracle()
+    u, v, t = make_events(w)
+    n, k, R = w["n"], w["k"], w["R"]
+    t0 = time.perf_counter()
+    H = oracle.hash_nodes(0, R, k, n)
+    hash_s = time.perf_counter() - t0
+    probe = 200_000
+    t0 = time.perf_counter()
+    oracle.proxy_matrices(u[:probe], v[:probe], t[:probe], H, k)
+    per_event = (time.perf_counter() - t0) / probe
+    ms = int(min(len(u), max(probe, args.cpu_seconds / max(per_event, 1e-12))))
+    ms = int(np.searchsorted(t, t[ms - 1], side="right")) if ms < len(u) else ms
+    t0 = time.perf_counter()
+    oracle.proxy_matrices(u[:ms], v[:ms], t[:ms], H, k)
+    spent = time.perf_counter() - t0
+    value = ms / spent
+    sample = f"hash tables ({hash_s:.1f} s, untimed) then the {R} proxy matrices over the first {ms} events, one thread"
+    line = {"impl": "reference", "metric": METRIC + " (hashed estimate)", "value": value, "unit": "events/s",
+            "n_gpus": world, "steps": 1, "warmup": 0, "ms_per_step": spent * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": w["desc"], "n": n, "m": w["m"], "k": k, "R": R},
+            "cpu_baseline": {"value": value, "unit": "events/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args, w, rank, world):
     if rank != 0:
         return
     if w["kind"] == "serving":
         run_reference_serving(args, w, world)
+        return
+    if w["kind"] == "hashed":
+        run_reference_hashed(args, w, world)
         return
     u, v, t = make_events(w)
     n = w["n"]
@@ -298,6 +338,140 @@ def run_serving(args, w, rank, world, local_rank):
         print(json.dumps(result), flush=True)
 
 
+def run_hashed(args, w, rank, world, local_rank):
+    """Network hashing end to end (Section 4): hash tables and super-events, the
+    R proxy schedules, the R proxy matrices in one persistent launch, the fused
+    estimate for the sampled sources, their exact out-sizes (component matrix
+    restricted to the sampled columns) and the error against them.  Beside the
+    step: the batched proxy launch replayed as a CUDA graph against the same R
+    proxies applied one launch at a time (identical matrices)."""
+    import torch
+    import paper_2307_04890_gb300 as tn
+    from paper_2307_04890_gb300.build import build_library
+
+    build_library()
+    tn.load_library()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    n, m, k, R, nsrc = w["n"], w["m"], w["k"], w["R"], w["nsrc"]
+    u, v, t = make_events(w, rank)
+    rng = np.random.default_rng(w["seed"] + 1000 * rank)
+    src_np = np.sort(rng.choice(n, nsrc, replace=False)).astype(np.uint32)
+    du = torch.from_numpy(u.view(np.int32)).to(dev)
+    dv = torch.from_numpy(v.view(np.int32)).to(dev)
+    dt = torch.from_numpy(t).to(dev)
+    src = torch.from_numpy(src_np.view(np.int32)).to(dev)
+    P = torch.empty((R, k, tn.tn_row_words(k)), dtype=torch.int64, device=dev)
+    Sx = torch.empty((n, tn.tn_row_words(nsrc)), dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    seed = 0  # replica j hashes with splitmix64(seed ^ j): seeds 0..R-1
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    timing = {"proxies_ms": [], "estimate_ms": [], "exact_ms": []}
+
+    def step(record):
+        H, pu, pv = tn.tn_hash_proxy(du, dv, n, k, R, seed)                              # a5
+        plans = [tn.Plan(pu[j].contiguous(), pv[j].contiguous(), dt, k) for j in range(R)]  # a1 (proxies)
+        plan_x = tn.Plan(du, dv, dt, n)                                                   # a1 (exact sample)
+        e = [ev() for _ in range(4)]
+        e[0].record(stream)
+        tn.tn_plan_apply_batch(plans, [P[j] for j in range(R)], init=True)                # a2 + a3 + a6
+        e[1].record(stream)
+        est = tn.tn_hash_estimate(P, R, k, H, n, src=src)                                 # a7
+        e[2].record(stream)
+        plan_x.apply(Sx, ncols=nsrc, src=src, init=True)                                  # a8: exact sampled columns
+        e[3].record(stream)
+        exact, _, _ = tn.tn_out_sizes(Sx, n, nsrc)
+        err = tn.tn_error_stats(est, exact, n)                                            # a8 (synchronises)
+        if record:
+            timing["proxies_ms"].append(e[0].elapsed_time(e[1]))
+            timing["estimate_ms"].append(e[1].elapsed_time(e[2]))
+            timing["exact_ms"].append(e[2].elapsed_time(e[3]))
+        for p in plans:
+            p.destroy()
+        plan_x.destroy()
+        return err, H, pu, pv
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches0 = tn.tn_kernel_launches()
+    start, end = ev(), ev()
+    with ClockSampler(torch.cuda.current_device()) as clocks:
+        torch.cuda.synchronize()
+        start.record(stream)
+        for _ in range(args.steps):
+            err, H, pu, pv = step(True)
+        end.record(stream)
+        torch.cuda.synchronize()
+    launches = tn.tn_kernel_launches() - launches0
+    ms_total = start.elapsed_time(end)
+    if dist:
+        tt = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_total = float(tt.item())
+    ms_step = ms_total / args.steps
+
+    # batched proxies: one graph replay vs R separate single-network launches
+    plans = [tn.Plan(pu[j].contiguous(), pv[j].contiguous(), dt, k) for j in range(R)]
+    g = tn.BatchGraph(plans, [P[j] for j in range(R)])
+    g.launch()
+    torch.cuda.synchronize()
+    ref = P.clone()
+    e0, e1 = ev(), ev()
+    e0.record(stream)
+    g.launch()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    graph_ms = e0.elapsed_time(e1)
+    P2 = torch.empty_like(P)
+    e0.record(stream)
+    for j in range(R):
+        plans[j].apply(P2[j], init=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    single_ms = e0.elapsed_time(e1)
+    identical = bool(torch.equal(P, ref) and torch.equal(P2, ref))
+    g.destroy()
+
+    proxy_ms = statistics.mean(timing["proxies_ms"])
+    exact_ms = statistics.mean(timing["exact_ms"])
+    wk, wx = tn.tn_row_words(k), tn.tn_row_words(nsrc)
+    alg_exact = m * 4 * ((nsrc + 63) // 64) * 8
+    alg_proxy = R * m * 4 * ((k + 63) // 64) * 8
+    peak, peak_kind = measured_peaks()
+    bit_updates = (R * k + nsrc) * m
+    result = {"metric": METRIC + " (hashed estimate)", "value": world * m / (ms_step * 1e-3), "unit": "events/s",
+              "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+              "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+              "data": "synthetic",
+              "config": {"workload": w["desc"], "n": n, "m": m, "k": k, "R": R, "sampled_sources": nsrc,
+                         "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                         "l2": "inputs larger than L2 (events 1.6 GB, sampled matrix %.1f GB)" % (n * wx * 8 / 1e9)},
+              "bit_updates_per_s": world * bit_updates / (ms_step * 1e-3),
+              "kernels_ms": {"proxies_batched": proxy_ms, "estimate": statistics.mean(timing["estimate_ms"]),
+                             "exact_sampled_columns": exact_ms},
+              "roofline": {"bound": "hbm", "kernel": "stream_kernel (exact sampled columns)",
+                           "achieved": alg_exact / (exact_ms * 1e-3) / 1e9, "peak": peak,
+                           "peak_source": f"{peak_kind} MEASURED_PEAKS hbm_gbs", "unit": "GB/s",
+                           "frac": alg_exact / (exact_ms * 1e-3) / 1e9 / peak, "traffic": None,
+                           "algorithmic_bytes_per_launch": alg_exact,
+                           "proxies_algorithmic_GBps": alg_proxy / (proxy_ms * 1e-3) / 1e9},
+              "error": {key: err[key] for key in ("mean_abs", "max_abs", "mean_rel", "max_rel", "w1")},
+              "batched_vs_single": {"graph_replay_ms": graph_ms, "single_launches_ms": single_ms,
+                                    "identical": identical},
+              "gpu_launches": launches, "clocks": clocks.summary()}
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse_args()
     w = WORKLOADS[args.workload]
@@ -306,6 +480,9 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if w["kind"] == "serving" and args.impl == "ours":
         run_serving(args, w, rank, world, local_rank)
+        return
+    if w["kind"] == "hashed" and args.impl == "ours":
+        run_hashed(args, w, rank, world, local_rank)
         return
     if args.impl == "reference":
         run_reference(args, w, rank, world)
