@@ -171,7 +171,8 @@ typedef struct tn_plan tn_plan;
 typedef struct tn_plan_options {
     uint32_t window_events; /* target events per scheduling window (0 = default 640) */
     uint32_t slab_words;    /* 64-bit words of every row owned by one CTA when the
-                               plan is applied: 2, 4, 8 or 16 (0 = default 16) */
+                               plan is applied: an even number from 2 to 16
+                               (0 = default 16) */
     uint32_t smem_rows;     /* row slots of the streaming kernel's shared-memory row
                                buffer (at most 160 KB / (8 slab_words)); windows with
                                more rows (plus saved copies) stream from global

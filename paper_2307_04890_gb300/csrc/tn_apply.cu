@@ -40,8 +40,8 @@ struct Job {
     uint64_t ld;    // row stride in words
     uint64_t *tmp;  // saved-row slots of global windows, ld words each
     int32_t *status;
-    uint32_t sw;    // slab words per CTA (power of two >= 2)
-    uint32_t lsw;   // log2(sw)
+    uint32_t sw;    // slab words per CTA (even, 2..16)
+    uint32_t cpr;   // 16-byte chunks of a row segment = sw / 2
     uint32_t cta_begin;
     uint32_t pad;
 };
@@ -63,6 +63,26 @@ __device__ inline uint32_t find_job(const JobList &jl, uint32_t cta)
     uint32_t j = 0;
     while (j + 1 < jl.count && jl.job[j + 1].cta_begin <= cta) ++j;
     return j;
+}
+
+// A consumer thread's place in the slab: `cpr` consecutive threads share one row
+// segment (one 16-byte chunk each) and `stride` row segments are handled at once.
+struct Lane {
+    uint32_t chunk, lane0, stride, cpr;
+    uint64_t col;  // first word of this thread's chunk
+    bool active;   // chunk inside the matrix and thread inside the row groups
+};
+
+__device__ inline Lane make_lane(const Job &J, uint32_t ct, uint64_t w0)
+{
+    Lane L;
+    L.cpr = J.cpr;
+    L.chunk = ct % L.cpr;
+    L.lane0 = ct / L.cpr;
+    L.stride = (uint32_t)kConsumers / L.cpr;
+    L.col = w0 + 2ull * L.chunk;
+    L.active = L.lane0 < L.stride && L.col < J.ld;
+    return L;
 }
 
 __device__ inline uint64_t *row_ptr(const Job &J, uint32_t ref, uint64_t col)
@@ -131,14 +151,12 @@ __device__ inline void apply_pull(const Job &J, uint32_t x, uint32_t b, uint64_t
     st_row16(pd, acc);
 }
 
-__device__ inline void apply_tile(const Job &J, const uint2 *ops, uint32_t count, uint32_t ct, uint64_t w0)
+__device__ inline void apply_tile(const Job &J, const uint2 *ops, uint32_t count, const Lane &L)
 {
-    const uint32_t cpr_log = J.lsw - 1;  // 16-byte chunks per row segment = sw/2
-    const uint32_t chunk = ct & ((1u << cpr_log) - 1u);
-    const uint64_t col = w0 + 2ull * chunk;
-    if (col >= J.ld) return;  // partial last slab
-    const uint32_t stride = (uint32_t)kConsumers >> cpr_log;
-    for (uint32_t o = ct >> cpr_log; o < count; o += 4 * stride) {
+    if (!L.active) return;  // partial last slab, or a thread outside the row groups
+    const uint64_t col = L.col;
+    const uint32_t stride = L.stride;
+    for (uint32_t o = L.lane0; o < count; o += 4 * stride) {
         uint2 op[4];
         bool live[4];
 #pragma unroll
@@ -171,7 +189,7 @@ __device__ inline void apply_tile(const Job &J, const uint2 *ops, uint32_t count
         }
     }
     // multi-source updates of tie groups (hub rows) in a second pass
-    for (uint32_t o = ct >> cpr_log; o < count; o += stride) {
+    for (uint32_t o = L.lane0; o < count; o += stride) {
         const uint2 op = ops[o];
         if ((op.x >> kKindShift) == kPull) apply_pull(J, op.x & kIdMask, op.y, col);
     }
@@ -181,17 +199,14 @@ __device__ inline void apply_tile(const Job &J, const uint2 *ops, uint32_t count
 // local record: the window's rows are gathered into shared memory, its levels
 // are applied there, and the rows are written back
 // ---------------------------------------------------------------------------
-__device__ inline void apply_record(const Job &J, const uint32_t *rec, u64x2 *buf, uint32_t ct, uint64_t w0)
+__device__ inline void apply_record(const Job &J, const uint32_t *rec, u64x2 *buf, const Lane &L)
 {
     const uint32_t D = rec[0], nlev = rec[2], nops = rec[3];
     const uint32_t *rows = rec + 4, *lvl = rows + D, *ops = lvl + nlev + 1, *aux = ops + nops;
-    const uint32_t cpr_log = J.lsw - 1;
-    const uint32_t cpr = 1u << cpr_log;
-    const uint32_t chunk = ct & (cpr - 1u);
-    const uint32_t lane0 = ct >> cpr_log, stride = (uint32_t)kConsumers >> cpr_log;
-    const uint64_t col = w0 + 2ull * chunk;
-    const bool active = col < J.ld;
-    u64x2 *mine = buf + chunk;  // slot q of this chunk lives at buf[q * cpr + chunk]
+    const uint32_t cpr = L.cpr, lane0 = L.lane0, stride = L.stride;
+    const uint64_t col = L.col;
+    const bool active = L.active;
+    u64x2 *mine = buf + L.chunk;  // slot q of this chunk lives at buf[q * cpr + chunk]
 
     if (active) {
         uint32_t d = lane0;
@@ -277,7 +292,7 @@ __global__ void __launch_bounds__(kThreads) stream_kernel(const __grid_constant_
     __shared__ int32_t gate;
 
     const Job &J = jl.job[find_job(jl, blockIdx.x)];
-    const uint64_t w0 = (uint64_t)(blockIdx.x - J.cta_begin) << J.lsw;
+    const uint64_t w0 = (uint64_t)(blockIdx.x - J.cta_begin) * J.sw;
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
     if (threadIdx.x == 0) {
         gate = *(volatile int32_t *)J.status;  // an earlier error gates this job
@@ -348,6 +363,7 @@ __global__ void __launch_bounds__(kThreads) stream_kernel(const __grid_constant_
     } else {
         // ---------------- consumers ----------------
         const uint32_t ct = threadIdx.x - 32;
+        const Lane L = make_lane(J, ct, w0);
         for (uint64_t it = 0;; ++it) {
             const int s = (int)(it % kStages);
             const uint32_t par = (uint32_t)(it / kStages) & 1u;
@@ -359,10 +375,10 @@ __global__ void __launch_bounds__(kThreads) stream_kernel(const __grid_constant_
             // item's loads, and all consumers agree on stopping
             if (consumers_sync_or(stop)) break;
             if (hdr[s].local) {
-                apply_record(J, reinterpret_cast<const uint32_t *>(stage + (size_t)s * kStageBytes), rowbuf, ct, w0);
+                apply_record(J, reinterpret_cast<const uint32_t *>(stage + (size_t)s * kStageBytes), rowbuf, L);
             } else {
                 apply_tile(J, reinterpret_cast<const uint2 *>(stage + (size_t)s * kStageBytes) + hdr[s].off,
-                           hdr[s].count, ct, w0);
+                           hdr[s].count, L);
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);
@@ -448,12 +464,6 @@ static int grid_for(uint64_t work)
     return (int)(g < 1 ? 1 : (g > 8192 ? 8192 : g));
 }
 
-static uint32_t log2u(uint32_t x)
-{
-    uint32_t l = 0;
-    while ((1u << l) < x) ++l;
-    return l;
-}
 
 tn_status apply_jobs(const tn_plan *const *plans, uint64_t *const *S, const uint32_t *ncols,
                      const uint32_t *const *src, int64_t *const *t_last, uint32_t count, uint32_t flags,
@@ -510,7 +520,7 @@ tn_status apply_jobs(const tn_plan *const *plans, uint64_t *const *S, const uint
             J.tmp = tmps[j];
             J.status = p->d_status;
             J.sw = sw;
-            J.lsw = log2u(sw);
+            J.cpr = sw / 2;
             J.cta_begin = ctas;
             ctas += (uint32_t)((ld + sw - 1) / sw);
         }

@@ -640,7 +640,7 @@ extern "C" tn_status tn_plan_create(const uint32_t *u, const uint32_t *v, const 
         if (opt->window_events) window = opt->window_events;
         rows = opt->smem_rows;
     }
-    if (sw != 2 && sw != 4 && sw != 8 && sw != 16) return TN_EINVAL;
+    if (sw < 2 || sw > 16 || (sw & 1u)) return TN_EINVAL;  // even: whole 16-byte chunks
     if (window < 32) window = 32;
     if (rows == 0) rows = kRowBufferBytes / (sw * 8);
     if (rows > kLocalSlotLimit) rows = kLocalSlotLimit;

@@ -101,7 +101,7 @@ def test_config1_full():
         assert np.array_equal(B[:, j], oracle.si_reach(u, v, t, n, int(j)))
 
 
-@pytest.mark.parametrize("slab", [2, 4, 8, 16])
+@pytest.mark.parametrize("slab", [2, 4, 6, 8, 10, 12, 14, 16])
 @pytest.mark.parametrize("window", [40, 700, 4096])
 def test_schedule_options_identical(slab, window):
     n = 1500  # several slabs, ragged last slab, several windows, ragged last window
@@ -114,14 +114,15 @@ def test_schedule_options_identical(slab, window):
     assert np.array_equal(host_matrix(S, n), oracle.component_matrix(u, v, t, n))
 
 
+@pytest.mark.parametrize("slab", [16, 12])
 @pytest.mark.parametrize("smem_rows", [1, 0, 1000])
-def test_local_and_global_windows_identical(smem_rows):
+def test_local_and_global_windows_identical(smem_rows, slab):
     """smem_rows=1 sends every window through the global-memory path; the
     default and a large buffer apply most windows in shared memory."""
     n = 5000
     u, v, t = synth.uniform_events(n, 60_000, t_range=25_000, seed=14)
     du, dv, dt = dev_events(u, v, t)
-    plan = tn.Plan(du, dv, dt, n, window_events=300, slab_words=8, smem_rows=smem_rows)
+    plan = tn.Plan(du, dv, dt, n, window_events=300, slab_words=slab, smem_rows=smem_rows)
     st = plan.stats()
     if smem_rows == 1:
         assert st["local_windows"] == 0
