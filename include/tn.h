@@ -254,7 +254,7 @@ tn_status tn_graph_destroy(tn_graph *graph);
  * depth, shared-memory row buffer = CTAs per SM) for a batch of `replicas`
  * networks shaped like (u, v, t, m, n), by timing every candidate on the
  * first `sample_events` events (0 = all) applied to `replicas` scratch
- * matrices.  Candidates: slab 2/4/8/16 words (at most the row width), window
+ * matrices.  Candidates: slab 2/4/8/12/16 words (at most the row width), window
  * 320/640/1024 events, row buffer 160 or 80 KB.  The choice is cached per
  * (device, n, replicas, floor(log2 m)) for the life of the process.  When the
  * scratch matrices would exceed 8 GiB nothing is timed and the defaults

@@ -176,7 +176,7 @@ extern "C" tn_status tn_autotune(const uint32_t *u, const uint32_t *v, const int
         TN_CUDA_TRY(cudaMallocAsync((void **)&p, (size_t)n * ld * 8, st));
         sc.mats.push_back(p);
     }
-    const uint32_t slabs[] = {2, 4, 8, 16};
+    const uint32_t slabs[] = {2, 4, 8, 12, 16};
     const uint32_t windows[] = {320, 640, 1024};
     float best = INFINITY;
     for (uint32_t sw : slabs) {

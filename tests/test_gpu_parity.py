@@ -115,7 +115,7 @@ def test_schedule_options_identical(slab, window):
 
 
 @pytest.mark.parametrize("slab", [16, 12])
-@pytest.mark.parametrize("smem_rows", [1, 0, 1000])
+@pytest.mark.parametrize("smem_rows", [1, 0, 600])
 def test_local_and_global_windows_identical(smem_rows, slab):
     """smem_rows=1 sends every window through the global-memory path; the
     default and a large buffer apply most windows in shared memory."""
