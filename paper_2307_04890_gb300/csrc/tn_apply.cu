@@ -43,7 +43,7 @@ struct Job {
     uint32_t sw;    // slab words per CTA (even, 2..16)
     uint32_t cpr;   // 16-byte chunks of a row segment = sw / 2
     uint32_t cta_begin;
-    uint32_t pad;
+    uint32_t dcap;  // row slots of the shared-memory row buffer
 };
 
 struct JobList {
@@ -151,7 +151,8 @@ __device__ inline void apply_pull(const Job &J, uint32_t x, uint32_t b, uint64_t
     st_row16(pd, acc);
 }
 
-__device__ inline void apply_tile(const Job &J, const uint2 *ops, uint32_t count, const Lane &L)
+// Direct form, for row buffers too small to stage a chunk: four ops in flight per thread.
+__device__ inline void apply_tile_direct(const Job &J, const uint2 *ops, uint32_t count, const Lane &L)
 {
     if (!L.active) return;  // partial last slab, or a thread outside the row groups
     const uint64_t col = L.col;
@@ -188,6 +189,60 @@ __device__ inline void apply_tile(const Job &J, const uint2 *ops, uint32_t count
             }
         }
     }
+    // multi-source updates of tie groups (hub rows) in a second pass
+    for (uint32_t o = L.lane0; o < count; o += stride) {
+        const uint2 op = ops[o];
+        if ((op.x >> kKindShift) == kPull) apply_pull(J, op.x & kIdMask, op.y, col);
+    }
+}
+
+// Ops of one level are independent: the row segments of a chunk of them are
+// first copied into shared memory (private slots 2i and 2i+1 for op i, so no
+// lookup is needed and every copy is in flight at once), then each op's
+// result goes from registers straight to its destination rows.
+__device__ inline void apply_tile(const Job &J, const uint2 *ops, uint32_t count, u64x2 *buf, uint32_t dcap,
+                                  const Lane &L)
+{
+    const uint32_t cpr = L.cpr, stride = L.stride;
+    const uint64_t col = L.col;
+    if (dcap < 64) {
+        apply_tile_direct(J, ops, count, L);
+        return;
+    }
+    const uint32_t chunk_ops = dcap / 2;
+    u64x2 *mine = buf + L.chunk;
+    for (uint32_t c0 = 0; c0 < count; c0 += chunk_ops) {
+        const uint32_t cn = count - c0 < chunk_ops ? count - c0 : chunk_ops;
+        if (L.active) {
+            for (uint32_t i = L.lane0; i < cn; i += stride) {
+                const uint2 op = ops[c0 + i];
+                const uint32_t kind = op.x >> kKindShift;
+                if (kind == kPull) continue;
+                if (kind != kCopy) cp_async16(mine + (2 * i) * cpr, J.S + (uint64_t)(op.x & kIdMask) * J.ld + col);
+                cp_async16(mine + (2 * i + 1) * cpr, J.S + (uint64_t)op.y * J.ld + col);
+            }
+        }
+        cp_async_wait_all();
+        consumers_sync();
+        if (L.active) {
+            for (uint32_t i = L.lane0; i < cn; i += stride) {
+                const uint2 op = ops[c0 + i];
+                const uint32_t kind = op.x >> kKindShift;
+                if (kind == kPull) continue;
+                const uint64_t ia = (uint64_t)(op.x & kIdMask) * J.ld + col;
+                const u64x2 rb = lds16(mine + (2 * i + 1) * cpr);
+                if (kind == kCopy) {
+                    st_row16(J.tmp + ia, rb);
+                } else {
+                    const u64x2 r = or16(lds16(mine + (2 * i) * cpr), rb);
+                    st_row16(J.S + ia, r);
+                    if (kind == kEvent) st_row16(J.S + (uint64_t)op.y * J.ld + col, r);
+                }
+            }
+        }
+        consumers_sync();  // the slots are reused by the next chunk
+    }
+    if (!L.active) return;
     // multi-source updates of tie groups (hub rows) in a second pass
     for (uint32_t o = L.lane0; o < count; o += stride) {
         const uint2 op = ops[o];
@@ -378,7 +433,7 @@ __global__ void __launch_bounds__(kThreads) stream_kernel(const __grid_constant_
                 apply_record(J, reinterpret_cast<const uint32_t *>(stage + (size_t)s * kStageBytes), rowbuf, L);
             } else {
                 apply_tile(J, reinterpret_cast<const uint2 *>(stage + (size_t)s * kStageBytes) + hdr[s].off,
-                           hdr[s].count, L);
+                           hdr[s].count, rowbuf, J.dcap, L);
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);
@@ -521,6 +576,7 @@ tn_status apply_jobs(const tn_plan *const *plans, uint64_t *const *S, const uint
             J.status = p->d_status;
             J.sw = sw;
             J.cpr = sw / 2;
+            J.dcap = p->dcap;
             J.cta_begin = ctas;
             ctas += (uint32_t)((ld + sw - 1) / sw);
         }
