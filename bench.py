@@ -60,6 +60,9 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--autotune", choices=["auto", "on", "off"], default="auto",
+                    help="pick plan options with tn_autotune before timing (auto: on for bursty and hashed)")
+    ap.add_argument("--tune-sample", type=int, default=2_000_000, help="events the autotuner times")
     ap.add_argument("--jobs", type=int, default=200, help="serving: number of jobs")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
     ap.add_argument("--max-active", type=int, default=16, help="serving: jobs resident at once")
@@ -370,12 +373,21 @@ def run_hashed(args, w, rank, world, local_rank):
     stream = torch.cuda.current_stream(dev)
     seed = 0  # replica j hashes with splitmix64(seed ^ j): seeds 0..R-1
     ev = lambda: torch.cuda.Event(enable_timing=True)
+    popts, xopts, tuned = {}, {}, None
+    if args.autotune in ("on", "auto"):
+        _, pu0, pv0 = tn.tn_hash_proxy(du, dv, n, k, R, seed)
+        tp = tn.tn_autotune(pu0[0].contiguous(), pv0[0].contiguous(), dt, k, replicas=R, sample_events=args.tune_sample)
+        tx = tn.tn_autotune(du, dv, dt, n, ncols=nsrc, sample_events=args.tune_sample)
+        popts = {key: tp[key] for key in ("window_events", "slab_words", "smem_rows")}
+        xopts = {key: tx[key] for key in ("window_events", "slab_words", "smem_rows")}
+        tuned = {"proxies": popts, "exact_sampled": xopts}
+        del pu0, pv0
     timing = {"proxies_ms": [], "estimate_ms": [], "exact_ms": []}
 
     def step(record):
         H, pu, pv = tn.tn_hash_proxy(du, dv, n, k, R, seed)                              # a5
-        plans = [tn.Plan(pu[j].contiguous(), pv[j].contiguous(), dt, k) for j in range(R)]  # a1 (proxies)
-        plan_x = tn.Plan(du, dv, dt, n)                                                   # a1 (exact sample)
+        plans = [tn.Plan(pu[j].contiguous(), pv[j].contiguous(), dt, k, **popts) for j in range(R)]  # a1 (proxies)
+        plan_x = tn.Plan(du, dv, dt, n, **xopts)                                          # a1 (exact sample)
         e = [ev() for _ in range(4)]
         e[0].record(stream)
         tn.tn_plan_apply_batch(plans, [P[j] for j in range(R)], init=True)                # a2 + a3 + a6
@@ -418,7 +430,7 @@ def run_hashed(args, w, rank, world, local_rank):
     ms_step = ms_total / args.steps
 
     # batched proxies: one graph replay vs R separate single-network launches
-    plans = [tn.Plan(pu[j].contiguous(), pv[j].contiguous(), dt, k) for j in range(R)]
+    plans = [tn.Plan(pu[j].contiguous(), pv[j].contiguous(), dt, k, **popts) for j in range(R)]
     g = tn.BatchGraph(plans, [P[j] for j in range(R)])
     g.launch()
     torch.cuda.synchronize()
@@ -451,6 +463,7 @@ def run_hashed(args, w, rank, world, local_rank):
               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
               "data": "synthetic",
               "config": {"workload": w["desc"], "n": n, "m": m, "k": k, "R": R, "sampled_sources": nsrc,
+                         "plan_options": tuned or "defaults",
                          "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                          "l2": "inputs larger than L2 (events 1.6 GB, sampled matrix %.1f GB)" % (n * wx * 8 / 1e9)},
               "bit_updates_per_s": world * bit_updates / (ms_step * 1e-3),
@@ -511,9 +524,14 @@ def main():
     stream = torch.cuda.current_stream(dev)
 
     k1_events = []
+    opts = dict(window_events=args.window, slab_words=args.slab, smem_rows=0)
+    tuned = None
+    if args.autotune == "on" or (args.autotune == "auto" and w["kind"] == "bursty"):
+        tuned = tn.tn_autotune(du, dv, dt, n, sample_events=args.tune_sample)
+        opts = {key: tuned[key] for key in ("window_events", "slab_words", "smem_rows")}
 
     def step(record):
-        plan = tn.Plan(du, dv, dt, n, window_events=args.window, slab_words=args.slab)  # a1
+        plan = tn.Plan(du, dv, dt, n, **opts)                                            # a1
         tn.tn_init_matrix(S, n)                                                          # a2
         if record:
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -570,7 +588,9 @@ def main():
               "config": {"workload": w["desc"], "n": n, "m": m, "global_batch": m * world,
                          "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                          "l2": "inputs larger than L2 (S %.2f GB, events %.0f MB)" % (n * W * 8 / 1e9, m * 16 / 1e6),
-                         "window_events": args.window or 640, "slab_words": args.slab or 16,
+                         "window_events": opts["window_events"] or 640, "slab_words": opts["slab_words"] or 16,
+                         "smem_rows": opts["smem_rows"] or "default",
+                         "autotuned": tuned is not None,
                          "levels": stats["levels"], "ops": stats["ops"]},
               "events_per_s": world * m / (ms_step * 1e-3),
               "roofline": roofline, "gpu_launches": launches, "clocks": clocks.summary(),

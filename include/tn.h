@@ -252,26 +252,29 @@ tn_status tn_graph_destroy(tn_graph *graph);
 /* ---------------------------------------------------------------------------
  * tn_autotune -- picks the plan options (slab width = columns per CTA, window
  * depth, shared-memory row buffer = CTAs per SM) for a batch of `replicas`
- * networks shaped like (u, v, t, m, n), by timing every candidate on the
- * first `sample_events` events (0 = all) applied to `replicas` scratch
- * matrices.  Candidates: slab 2/4/8/12/16 words (at most the row width), window
- * 320/640/1024 events, row buffer 160 or 80 KB.  The choice is cached per
- * (device, n, replicas, floor(log2 m)) for the life of the process.  When the
- * scratch matrices would exceed 8 GiB nothing is timed and the defaults
- * (all-zero options) are returned with tried = 0.  Synchronous.
+ * networks shaped like (u, v, t, m, n), each with `ncols` source columns
+ * (0 = n; fewer = a column subset as in tn_component_columns).  The full problem runs replicas x
+ * ceil(row words / slab) CTAs in waves of (SMs x CTAs per SM); every candidate
+ * is timed on the first `sample_events` events (0 = all) over one wave's worth
+ * of CTAs -- whole scratch matrices for small n, the first source columns for
+ * large n (columns are independent) -- and scored as waves x that time.
+ * Candidates: slab 2/4/8/12/16 words (at most the row width), window
+ * 320/640/1024 events, row buffer 160 or 80 KB.  Scratch of one timing run is
+ * kept under 4 GiB.  The choice is cached per (device, n, replicas,
+ * floor(log2 m)) for the life of the process.  Synchronous.
  */
 typedef struct tn_tune_result {
     tn_plan_options best;   /* options to pass to tn_plan_create */
-    float best_ms;          /* batched apply time of the sample with them */
-    uint32_t tried;         /* candidates timed (0: defaults, not timed) */
+    float best_ms;          /* its score: waves x timed sample (ms) */
+    uint32_t tried;         /* candidates timed */
     uint32_t cached;        /* 1 if the result came from the cache */
     uint32_t pad;
     uint64_t sample_events;
 } tn_tune_result;
 
 tn_status tn_autotune(const uint32_t *u, const uint32_t *v, const int64_t *t, uint64_t m,
-                      uint32_t n, uint32_t replicas, uint64_t sample_events, void *stream,
-                      tn_tune_result *result);
+                      uint32_t n, uint32_t ncols, uint32_t replicas, uint64_t sample_events,
+                      void *stream, tn_tune_result *result);
 
 /* ---------------------------------------------------------------------------
  * tn_hash_proxy -- network hashing (Section 4.1).

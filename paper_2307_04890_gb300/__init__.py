@@ -123,7 +123,7 @@ def load_library(path: str | None = None):
         "tn_graph_capture_batch": ([vp, vp, vp, u32, u32, ctypes.POINTER(vp)], i32),
         "tn_graph_launch": ([vp, vp], i32),
         "tn_graph_destroy": ([vp], i32),
-        "tn_autotune": ([vp, vp, vp, u64, u32, u32, u64, vp, ctypes.POINTER(_TuneResult)], i32),
+        "tn_autotune": ([vp, vp, vp, u64, u32, u32, u32, u64, vp, ctypes.POINTER(_TuneResult)], i32),
         "tn_server_create": ([ctypes.POINTER(_ServerOptions), ctypes.POINTER(vp)], i32),
         "tn_server_submit": ([vp, u64, u32, vp, vp, vp, vp, u32, vp, vp], i32),
         "tn_server_poll": ([vp, ctypes.POINTER(_JobRecord), u32, ctypes.POINTER(u32), u32], i32),
@@ -468,13 +468,15 @@ class Server:
         self.close()
 
 
-def tn_autotune(u, v, t, n: int, replicas: int = 1, sample_events: int = 200_000, stream=None) -> dict:
-    """Plan options for a batch of ``replicas`` networks shaped like (u, v, t, n),
-    chosen by timing the candidates on the first ``sample_events`` events."""
+def tn_autotune(u, v, t, n: int, replicas: int = 1, sample_events: int = 200_000, ncols: int = 0,
+                stream=None) -> dict:
+    """Plan options for a batch of ``replicas`` networks shaped like (u, v, t, n)
+    with ``ncols`` source columns each (0 = n), chosen by timing the candidates
+    on the first ``sample_events`` events (scored as waves x one wave's time)."""
     lib = load_library()
     m = _events(u, v, t)
     res = _TuneResult()
-    _check(lib.tn_autotune(_ptr(u), _ptr(v), _ptr(t), m, n, replicas, sample_events, _stream(stream),
+    _check(lib.tn_autotune(_ptr(u), _ptr(v), _ptr(t), m, n, ncols, replicas, sample_events, _stream(stream),
                            ctypes.byref(res)), "tn_autotune")
     return {"window_events": res.best.window_events, "slab_words": res.best.slab_words,
             "smem_rows": res.best.smem_rows, "best_ms": res.best_ms, "tried": res.tried,

@@ -101,26 +101,15 @@ extern "C" tn_status tn_graph_destroy(tn_graph *g)
 namespace {
 
 std::mutex g_tune_mu;
-std::map<std::tuple<int, uint32_t, uint32_t, int>, tn_tune_result> g_tune_cache;
+std::map<std::tuple<int, uint32_t, uint32_t, uint32_t, int>, tn_tune_result> g_tune_cache;
 
-constexpr uint64_t kTuneBytesLimit = 8ull << 30;  // scratch matrices of one tuning run
+constexpr uint64_t kTuneBytesLimit = 4ull << 30;  // scratch matrices of one timing run
 
-struct Scratch {
-    std::vector<uint64_t *> mats;
-    cudaStream_t st;
-    ~Scratch()
-    {
-        for (uint64_t *p : mats)
-            if (p) cudaFreeAsync(p, st);
-    }
-};
-
-// Time of one batched application of `plan` to every scratch matrix (best of 2).
-tn_status time_apply(tn_plan *plan, const Scratch &sc, uint32_t n, cudaStream_t st, float *ms)
+// Time of one batched application of `plan` to `count` matrices of `ncols`
+// columns (the first ncols node ids as sources when ncols < n), best of 2.
+tn_status time_apply(tn_plan *plan, uint64_t *const *mats, uint32_t count, uint32_t ncols, const uint32_t *src,
+                     cudaStream_t st, float *ms)
 {
-    const uint32_t count = (uint32_t)sc.mats.size();
-    std::vector<const tn_plan *> plans(count, plan);
-    std::vector<uint32_t> ncols(count, n);
     cudaEvent_t e0, e1;
     TN_CUDA_TRY(cudaEventCreate(&e0));
     TN_CUDA_TRY(cudaEventCreate(&e1));
@@ -128,7 +117,12 @@ tn_status time_apply(tn_plan *plan, const Scratch &sc, uint32_t n, cudaStream_t 
     tn_status rc = TN_OK;
     for (int rep = 0; rep < 2 && rc == TN_OK; ++rep) {
         cudaEventRecord(e0, st);
-        rc = tn_plan_apply_batch(plans.data(), sc.mats.data(), ncols.data(), count, TN_INIT_IDENTITY, st);
+        for (uint32_t r = 0; r < count && rc == TN_OK; ++r)
+            if (src) rc = tn_init_matrix(mats[r], plan->n, ncols, src, st);
+        std::vector<const tn_plan *> plans(count, plan);
+        std::vector<uint32_t> nc(count, ncols);
+        if (rc == TN_OK)
+            rc = tn_plan_apply_batch(plans.data(), mats, nc.data(), count, src ? 0u : TN_INIT_IDENTITY, st);
         cudaEventRecord(e1, st);
         if (cudaEventSynchronize(e1) != cudaSuccess) rc = TN_ECUDA;
         float t = 0.f;
@@ -142,16 +136,25 @@ tn_status time_apply(tn_plan *plan, const Scratch &sc, uint32_t n, cudaStream_t 
 
 }  // namespace
 
+// The full problem (replicas x ceil(row words / slab) CTAs) runs in waves of
+// SMs x CTAs-per-SM; every candidate is timed on one wave's worth of CTAs --
+// whole matrices for small networks, a subset of source columns for large ones
+// (columns are independent, so a CTA's work does not depend on the others) --
+// and scored as waves x that time.
 extern "C" tn_status tn_autotune(const uint32_t *u, const uint32_t *v, const int64_t *t, uint64_t m, uint32_t n,
-                                 uint32_t replicas, uint64_t sample_events, void *stream, tn_tune_result *out)
+                                 uint32_t ncols_full, uint32_t replicas, uint64_t sample_events, void *stream,
+                                 tn_tune_result *out)
 {
-    if (!u || !v || !t || m == 0 || n == 0 || n >= (1u << 30) || replicas == 0 || replicas > 64 || !out)
+    if (ncols_full == 0) ncols_full = n;
+    if (!u || !v || !t || m == 0 || n == 0 || n >= (1u << 30) || replicas == 0 || replicas > 64 || !out ||
+        ncols_full > n)
         return TN_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
-    int dev = 0;
+    int dev = 0, nsm = 0;
     TN_CUDA_TRY(cudaGetDevice(&dev));
+    TN_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     const int mb = (int)floor(log2((double)m));
-    const auto key = std::make_tuple(dev, n, replicas, mb);
+    const auto key = std::make_tuple(dev, n, ncols_full, replicas, mb);
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tune_cache.find(key);
@@ -162,49 +165,86 @@ extern "C" tn_status tn_autotune(const uint32_t *u, const uint32_t *v, const int
         }
     }
     memset(out, 0, sizeof(*out));
-    const uint64_t ld = tn_row_words(n);
-    const uint64_t ms = sample_events && sample_events < m ? sample_events : m;
-    out->sample_events = ms;
-    if ((uint64_t)replicas * n * ld * 8 > kTuneBytesLimit) {
-        // too large to time here: keep the defaults
-        return TN_OK;
-    }
-    Scratch sc;
-    sc.st = st;
-    for (uint32_t r = 0; r < replicas; ++r) {
-        uint64_t *p = nullptr;
-        TN_CUDA_TRY(cudaMallocAsync((void **)&p, (size_t)n * ld * 8, st));
-        sc.mats.push_back(p);
-    }
+    const uint64_t ld = tn_row_words(ncols_full);
+    const uint64_t msample = sample_events && sample_events < m ? sample_events : m;
+    out->sample_events = msample;
+
+    // source ids 0..max-1 for column-subset timings
+    const uint32_t max_cols = (uint32_t)nsm * 2u * 16u * 64u;
+    uint32_t *ids = nullptr;
+    std::vector<uint32_t> hids(max_cols);
+    for (uint32_t i = 0; i < max_cols; ++i) hids[i] = i;
+    TN_CUDA_TRY(cudaMallocAsync((void **)&ids, max_cols * sizeof(uint32_t), st));
+    TN_CUDA_TRY(cudaMemcpyAsync(ids, hids.data(), max_cols * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+    TN_CUDA_TRY(cudaStreamSynchronize(st));
+
     const uint32_t slabs[] = {2, 4, 8, 12, 16};
     const uint32_t windows[] = {320, 640, 1024};
     float best = INFINITY;
+    tn_status rc = TN_OK;
     for (uint32_t sw : slabs) {
-        if (sw > ld) continue;
-        for (uint32_t win : windows) {
-            for (int half = 0; half < 2; ++half) {
+        if (sw > ld || rc != TN_OK) continue;
+        for (int half = 0; half < 2 && rc == TN_OK; ++half) {
+            const uint64_t occ = half ? 2 : 1;  // 32 KB of stages + 80 or 160 KB of rows per CTA
+            const uint64_t per_rep = (ld + sw - 1) / sw;
+            const uint64_t total = per_rep * replicas;
+            const uint64_t slots = (uint64_t)nsm * occ;
+            const uint64_t waves = (total + slots - 1) / slots;
+            // one wave's worth of CTAs
+            uint32_t reps = 1, ncols = ncols_full;
+            const uint32_t *src = ncols_full < n ? ids : nullptr;
+            if (per_rep >= slots) {
+                uint64_t c = slots;
+                while (c > 1 && (uint64_t)n * tn_row_words(c * sw * 64) * 8 > kTuneBytesLimit) c /= 2;
+                if (c * sw * 64 < ncols_full) {
+                    ncols = (uint32_t)(c * sw * 64);
+                    src = ids;
+                }
+            } else {
+                reps = (uint32_t)((slots + per_rep - 1) / per_rep);
+                if (reps > replicas) reps = replicas;
+                while (reps > 1 && (uint64_t)reps * n * ld * 8 > kTuneBytesLimit) --reps;
+                if ((uint64_t)n * ld * 8 > kTuneBytesLimit) continue;
+                if (src && ncols > max_cols) continue;
+            }
+            std::vector<uint64_t *> mats(reps, nullptr);
+            const uint64_t mbytes = (uint64_t)n * tn_row_words(ncols) * 8;
+            for (uint32_t r = 0; r < reps && rc == TN_OK; ++r) {
+                const cudaError_t e = cudaMallocAsync((void **)&mats[r], mbytes, st);
+                if (e != cudaSuccess) {
+                    tn_internal_set_cuda_error(e);
+                    rc = e == cudaErrorMemoryAllocation ? TN_ENOMEM : TN_ECUDA;
+                }
+            }
+            for (uint32_t win : windows) {
+                if (rc != TN_OK) break;
                 tn_plan_options opt;
                 memset(&opt, 0, sizeof(opt));
                 opt.window_events = win;
                 opt.slab_words = sw;
                 opt.smem_rows = (half ? 80u : 160u) * 1024u / (8u * sw);
                 tn_plan *plan = nullptr;
-                tn_status rc = tn_plan_create(u, v, t, ms, n, nullptr, &opt, st, &plan);
-                if (rc != TN_OK) return rc;
+                rc = tn_plan_create(u, v, t, msample, n, nullptr, &opt, st, &plan);
+                if (rc != TN_OK) break;
                 float tms = INFINITY;
-                rc = time_apply(plan, sc, n, st, &tms);
+                rc = time_apply(plan, mats.data(), reps, ncols, src, st, &tms);
                 if (rc == TN_OK) rc = tn_plan_status(plan, st);
                 tn_plan_destroy(plan, st);
-                if (rc != TN_OK) return rc;
+                if (rc != TN_OK) break;
                 out->tried++;
-                if (tms < best) {
-                    best = tms;
+                const float score = tms * (float)waves;
+                if (score < best) {
+                    best = score;
                     out->best = opt;
-                    out->best_ms = tms;
+                    out->best_ms = score;
                 }
             }
+            for (uint64_t *p : mats)
+                if (p) cudaFreeAsync(p, st);
         }
     }
+    cudaFreeAsync(ids, st);
+    if (rc != TN_OK) return rc;
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_tune_cache[key] = *out;
     return TN_OK;
