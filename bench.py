@@ -377,10 +377,9 @@ def run_hashed(args, w, rank, world, local_rank):
     if args.autotune in ("on", "auto"):
         _, pu0, pv0 = tn.tn_hash_proxy(du, dv, n, k, R, seed)
         tp = tn.tn_autotune(pu0[0].contiguous(), pv0[0].contiguous(), dt, k, replicas=R, sample_events=args.tune_sample)
-        tx = tn.tn_autotune(du, dv, dt, n, ncols=nsrc, sample_events=args.tune_sample)
         popts = {key: tp[key] for key in ("window_events", "slab_words", "smem_rows")}
-        xopts = {key: tx[key] for key in ("window_events", "slab_words", "smem_rows")}
-        tuned = {"proxies": popts, "exact_sampled": xopts}
+        # the sampled exact columns keep the defaults: 64 CTAs of 16-word slabs in one wave
+        tuned = {"proxies": popts, "exact_sampled": "defaults"}
         del pu0, pv0
     timing = {"proxies_ms": [], "estimate_ms": [], "exact_ms": []}
 
