@@ -393,7 +393,8 @@ typedef struct tn_server_options {
     uint64_t memory_budget; /* device bytes for resident jobs (0 = 60 % of free memory) */
     uint32_t max_active;    /* jobs resident at once (0 = 16) */
     uint32_t window_events; /* plan options of every batch (0 = defaults) */
-    uint32_t slab_words;
+    uint32_t slab_words;    /* 0 = per job: the widest even slab (at most 16 words)
+                               that still gives the job 16 CTAs, at least 2 words */
     uint32_t reserved[3];   /* must be zero */
 } tn_server_options;
 

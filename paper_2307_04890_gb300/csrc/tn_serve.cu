@@ -107,6 +107,18 @@ void release_job(ServeJob *j)
         }                                         \
     } while (0)
 
+// Slab width of a job when the server options leave it open: a small matrix
+// still gets at least 16 CTAs (every CTA streams all of the job's events, so
+// narrower slabs shorten the job), large ones keep 16-word slabs.
+uint32_t serve_slab_words(uint32_t n)
+{
+    const uint64_t ld = tn_row_words(n);
+    uint64_t sw = ld / 16;
+    if (sw > 16) sw = 16;
+    sw &= ~1ull;
+    return sw < 2 ? 2u : (uint32_t)sw;
+}
+
 // Copies the job in, schedules every batch and enqueues the whole job on its
 // stream.  Runs on the worker thread.
 tn_status start_job(tn_server *s, ServeJob *j)
@@ -133,7 +145,7 @@ tn_status start_job(tn_server *s, ServeJob *j)
     tn_plan_options opt;
     memset(&opt, 0, sizeof(opt));
     opt.window_events = s->opt.window_events;
-    opt.slab_words = s->opt.slab_words;
+    opt.slab_words = s->opt.slab_words ? s->opt.slab_words : serve_slab_words(j->n);
     tn_status rc = TN_OK;
     for (uint32_t b = 0; b < nb && rc == TN_OK; ++b) {
         const uint64_t e0 = j->offs[b], mb = j->offs[b + 1] - e0;
