@@ -374,7 +374,7 @@ tn_status tn_hash_estimate_noalloc(const uint64_t *P, uint32_t R, uint32_t k, co
  * Serving (Section 3.5: the method is a one-pass streaming algorithm, so a
  * job's matrix can stay on the device while its event batches arrive).
  *
- * A server runs a worker thread on the device that is current when it is
+ * A server runs worker threads on the device that is current when it is
  * created.  tn_server_submit queues a job; the worker admits queued jobs in
  * arrival order whenever fewer than max_active jobs are resident and the
  * job's device memory (matrix + schedules, estimated at submit) fits in

@@ -29,6 +29,18 @@ void tn_internal_keep_pool(void)
     }
     done[dev] = true;
 }
+cudaError_t tn_internal_allow_max_dyn_smem(const void *kernel)
+{
+    int dev = 0, optin = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (err == cudaSuccess) err = cudaFuncGetAttributes(&fa, kernel);
+    if (err == cudaSuccess)
+        err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+    return err;
+}
+
 static std::atomic<uint64_t> g_launches{0};
 void tn_internal_count_launches(uint64_t count) { g_launches.fetch_add(count, std::memory_order_relaxed); }
 extern "C" uint64_t tn_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }

@@ -582,7 +582,7 @@ tn_status apply_jobs(const tn_plan *const *plans, uint64_t *const *S, const uint
         }
         TN_CUDA_TRY(cudaGetLastError());
         if (ctas) {
-            TN_CUDA_TRY(cudaFuncSetAttribute(stream_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            TN_CUDA_TRY(tn_internal_allow_max_dyn_smem((const void *)stream_kernel));
             tn_internal_count_launches(1);
             stream_kernel<<<ctas, kThreads, smem, st>>>(jl);
         }

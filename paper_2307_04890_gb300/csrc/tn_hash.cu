@@ -349,7 +349,7 @@ extern "C" tn_status tn_hash_estimate(const uint64_t *P, uint32_t R, uint32_t k,
     size_t smem = 0;
     if (table_bytes <= 200 * 1024) {
         smem = table_bytes;
-        TN_CUDA_TRY(cudaFuncSetAttribute(estimate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        TN_CUDA_TRY(tn_internal_allow_max_dyn_smem((const void *)estimate_kernel));
     } else {
         TN_CUDA_TRY(cudaMallocAsync((void **)&gtable, table_bytes * batches, st));  // one table per CTA
     }
@@ -428,7 +428,7 @@ extern "C" tn_status tn_hash_estimate_noalloc(const uint64_t *P, uint32_t R, uin
     uint8_t *gtable = nullptr;
     if (smem_table) {
         smem = table_bytes;
-        TN_CUDA_TRY(cudaFuncSetAttribute(estimate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        TN_CUDA_TRY(tn_internal_allow_max_dyn_smem((const void *)estimate_kernel));
     } else {
         gtable = scratch + kNoallocTableOffset;  // every byte is written by its CTA before it is read
     }

@@ -19,6 +19,10 @@ void tn_internal_set_cuda_error(cudaError_t err);
 // Keeps memory freed to the current device's stream-ordered pool cached for
 // reuse instead of returning it to the driver at every synchronisation.
 void tn_internal_keep_pool(void);
+// Raises a kernel's dynamic shared-memory limit to everything the device allows
+// beside the kernel's static shared memory.  Always the same value for a given
+// kernel, so concurrent callers (threads, streams) cannot undo each other.
+cudaError_t tn_internal_allow_max_dyn_smem(const void *kernel);
 // Adds `count` to the process-wide kernel launch counter (tn_kernel_launches).
 void tn_internal_count_launches(uint64_t count);
 

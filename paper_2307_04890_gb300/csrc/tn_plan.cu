@@ -717,7 +717,7 @@ extern "C" tn_status tn_plan_create(const uint32_t *u, const uint32_t *v, const 
     TN_STEP(alloc_async(&a.big_arena, host_counters[2], st));
     {
         const size_t smem = arena_words(host_counters[3] ? host_counters[3] : 1) * 4;
-        TN_STEP(cudaFuncSetAttribute(schedule_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        TN_STEP(tn_internal_allow_max_dyn_smem((const void *)schedule_smem_kernel));
         tn_internal_count_launches(1);
         schedule_smem_kernel<<<a.nw, kPlanThreads, smem, st>>>(a);
         if (host_counters[1]) {

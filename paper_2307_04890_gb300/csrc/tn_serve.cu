@@ -32,6 +32,8 @@
 
 namespace {
 
+constexpr int kServeWorkers = 4;
+
 uint64_t now_ns()
 {
     return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
@@ -72,8 +74,9 @@ struct tn_server {
     std::condition_variable finished_cv;
     uint64_t in_use = 0;
     uint64_t admitted = 0, completed = 0, peak_active = 0, peak_bytes = 0;
+    uint64_t starting = 0;  // jobs admitted whose start is in progress
     bool stop = false;
-    std::thread worker;
+    std::vector<std::thread> workers;
 };
 
 namespace {
@@ -230,17 +233,20 @@ void worker_loop(tn_server *s)
             ServeJob *j = nullptr;
             {
                 std::lock_guard<std::mutex> lock(s->mu);
-                if (s->queue.empty() || s->active.size() >= s->opt.max_active) break;
+                const uint64_t resident = s->active.size() + s->starting;
+                if (s->queue.empty() || resident >= s->opt.max_active) break;
                 ServeJob *head = s->queue.front();
-                if (s->in_use + head->bytes > s->budget && !s->active.empty()) break;
+                if (s->in_use + head->bytes > s->budget && resident > 0) break;
                 s->queue.pop_front();
                 s->in_use += head->bytes;
                 s->admitted++;
+                s->starting++;
                 j = head;
             }
             j->t_admit = now_ns();
             j->status = start_job(s, j);
             std::lock_guard<std::mutex> lock(s->mu);
+            s->starting--;
             s->active.push_back(j);
             if (s->active.size() > s->peak_active) s->peak_active = s->active.size();
             if (s->in_use > s->peak_bytes) s->peak_bytes = s->in_use;
@@ -266,7 +272,7 @@ void worker_loop(tn_server *s)
         progressed = progressed || !done.empty();
         {
             std::unique_lock<std::mutex> lock(s->mu);
-            if (s->stop && s->queue.empty() && s->active.empty()) return;
+            if (s->stop && s->queue.empty() && s->active.empty() && s->starting == 0) return;
             if (!progressed) {
                 if (s->active.empty()) {
                     s->cv.wait_for(lock, std::chrono::milliseconds(5));
@@ -299,7 +305,10 @@ extern "C" tn_status tn_server_create(const tn_server_options *opt, tn_server **
     }
     tn_internal_keep_pool();
     s->budget = s->opt.memory_budget ? s->opt.memory_budget : (uint64_t)(free_b * 0.6);
-    s->worker = std::thread(worker_loop, s);
+    // several workers, so that copying in and scheduling one job (host
+    // synchronisations on its own stream) does not hold up the admission of
+    // the next ones
+    for (int w = 0; w < kServeWorkers; ++w) s->workers.emplace_back(worker_loop, s);
     *out = s;
     return TN_OK;
 }
@@ -386,7 +395,8 @@ extern "C" tn_status tn_server_destroy(tn_server *s)
         s->stop = true;
     }
     s->cv.notify_all();
-    if (s->worker.joinable()) s->worker.join();
+    for (std::thread &w : s->workers)
+        if (w.joinable()) w.join();
     delete s;
     return TN_OK;
 }
