@@ -71,11 +71,27 @@ def parse_args():
 
 def make_events(w, rank=0):
     from paper_2307_04890_gb300 import synth
+    seed = replica_seed(w, rank)
     if w["kind"] in ("activity", "hashed"):
-        return synth.activity_driven(w["n"], w["m"], seed=w["seed"] + 1000 * rank)
+        return synth.activity_driven(w["n"], w["m"], seed=seed)
     if w["kind"] == "bursty":
-        return synth.powerlaw_bursty(w["n"], w["m"], seed=w["seed"] + 1000 * rank)
-    return synth.uniform_events(w["n"], w["m"], t_range=w["t_range"], seed=w["seed"] + 1000 * rank)
+        return synth.powerlaw_bursty(w["n"], w["m"], seed=seed)
+    return synth.uniform_events(w["n"], w["m"], t_range=w["t_range"], seed=seed)
+
+
+def replica_seed(w, rank):
+    """Rank r runs an independent replica of the workload (weak scaling), seeded apart."""
+    return w["seed"] + 1000 * rank
+
+
+def job_max_ms(ms, dist, device):
+    """The job's time is its slowest rank's: all-reduce MAX over ranks (no-op alone)."""
+    if dist is None:
+        return ms
+    import torch
+    tt = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
 
 
 def measured_peaks():
@@ -421,11 +437,7 @@ def run_hashed(args, w, rank, world, local_rank):
         end.record(stream)
         torch.cuda.synchronize()
     launches = tn.tn_kernel_launches() - launches0
-    ms_total = start.elapsed_time(end)
-    if dist:
-        tt = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_total = float(tt.item())
+    ms_total = job_max_ms(start.elapsed_time(end), dist, dev)
     ms_step = ms_total / args.steps
 
     # batched proxies: one graph replay vs R separate single-network launches
@@ -561,11 +573,7 @@ def main():
     if dist:
         dist.barrier()
     launches = tn.tn_kernel_launches() - launches0
-    ms_total = start.elapsed_time(end)
-    if dist:
-        tt = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_total = float(tt.item())
+    ms_total = job_max_ms(start.elapsed_time(end), dist, dev)
     ms_step = ms_total / args.steps
     k1_ms = sum(a.elapsed_time(b) for a, b in k1_events) / len(k1_events)
     value = world * n * m / (ms_step * 1e-3)
