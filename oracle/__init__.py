@@ -9,6 +9,7 @@ arrays.  Functions cite the paper passage they follow:
 
 * ``component_matrix``  -- Algorithm 1 (Section 3.1) with equal-timestamp
   groups applied as snapshots (adjacency needs dt > 0, Section 2.1).
+* ``component_matrix_reversed`` -- the reversed-sequence variant (Section 3.4).
 * ``si_reach``          -- the deterministic SI process (Section 1).
 * ``column_counts`` / ``row_counts`` / ``argmax`` -- component sizes
   (Section 3.1, eq. for the mean size s_t in Section 3.3).
@@ -65,6 +66,8 @@ def _load():
         lib.tnref_apply_events.argtypes = [_u32p, _u32p, _i64p, ctypes.c_uint64, ctypes.c_uint32,
                                            _u64p, ctypes.c_uint64]
         lib.tnref_apply_events.restype = ctypes.c_int
+        lib.tnref_apply_events_reversed.argtypes = lib.tnref_apply_events.argtypes
+        lib.tnref_apply_events_reversed.restype = ctypes.c_int
         lib.tnref_si_reach.argtypes = [_u32p, _u32p, _i64p, ctypes.c_uint64, ctypes.c_uint32,
                                        ctypes.c_uint32, _u8p]
         lib.tnref_si_reach.restype = ctypes.c_int
@@ -146,6 +149,15 @@ def component_matrix(u, v, t, n, src=None) -> np.ndarray:
     """Component matrix from the identity (or from the listed source columns)."""
     S = init_sources(n, src)
     return apply_events(u, v, t, n, S)
+
+
+def component_matrix_reversed(u, v, t, n) -> np.ndarray:
+    """Reversed-sequence variant (Section 3.4): the identity, then the timestamp
+    groups from the last to the first; row i ends as the out-component of i."""
+    u, v, t = _ev(u, v, t)
+    S = init_sources(n)
+    _check(_load().tnref_apply_events_reversed(u, v, t, len(u), n, S.reshape(-1), S.shape[1]))
+    return S
 
 
 def si_reach(u, v, t, n, source) -> np.ndarray:

@@ -87,77 +87,110 @@ void tnref_init_sources(uint64_t *S, uint32_t n, uint64_t width,
  * Because S[a] already contains old[a], a singleton group gives
  * S[a] = S[b] = old[a] | old[b], which is Algorithm 1's update.
  * ------------------------------------------------------------------------- */
-int tnref_apply_events(const uint32_t *u, const uint32_t *v, const int64_t *t,
-                       uint64_t m, uint32_t n, uint64_t *S, uint64_t width)
+/* One timestamp group [g0, g1) applied as a snapshot: every endpoint's row
+ * gets the OR of its partners' rows as they were before the group. */
+struct tnref_groups {
+    int64_t *slot;
+    uint32_t *touched;
+    uint64_t *old;
+    uint64_t cap;
+};
+
+static int apply_group(struct tnref_groups *gs, const uint32_t *u, const uint32_t *v, uint64_t g0,
+                       uint64_t g1, uint64_t *S, uint64_t width)
+{
+    uint64_t need = 2 * (g1 - g0);
+    if (need > gs->cap) {
+        free(gs->touched);
+        free(gs->old);
+        gs->cap = need;
+        gs->touched = (uint32_t *)malloc(gs->cap * sizeof(uint32_t));
+        gs->old = (uint64_t *)malloc(gs->cap * width * sizeof(uint64_t));
+        if (!gs->touched || !gs->old)
+            return TNREF_ENOMEM;
+    }
+    /* snapshot the rows of the group's nodes */
+    uint64_t nt = 0;
+    for (uint64_t e = g0; e < g1; ++e) {
+        uint32_t ends[2] = {u[e], v[e]};
+        for (int q = 0; q < 2; ++q) {
+            uint32_t x = ends[q];
+            if (gs->slot[x] < 0) {
+                gs->slot[x] = (int64_t)nt;
+                gs->touched[nt] = x;
+                memcpy(gs->old + nt * width, S + (uint64_t)x * width, width * sizeof(uint64_t));
+                ++nt;
+            }
+        }
+    }
+    /* OR the partners' old rows into each endpoint */
+    for (uint64_t e = g0; e < g1; ++e) {
+        uint64_t *ra = S + (uint64_t)u[e] * width;
+        uint64_t *rb = S + (uint64_t)v[e] * width;
+        const uint64_t *oa = gs->old + (uint64_t)gs->slot[u[e]] * width;
+        const uint64_t *ob = gs->old + (uint64_t)gs->slot[v[e]] * width;
+        for (uint64_t w = 0; w < width; ++w) {
+            ra[w] |= ob[w];
+            rb[w] |= oa[w];
+        }
+    }
+    for (uint64_t k = 0; k < nt; ++k)
+        gs->slot[gs->touched[k]] = -1;
+    return TNREF_OK;
+}
+
+/* Algorithm 1 with group snapshots, in chronological order (reverse = 0) or,
+ * for the reversed-sequence variant of Section 3.4, from the last group to
+ * the first (reverse = 1): then row i ends as the out-component of i. */
+static int apply_events_dir(const uint32_t *u, const uint32_t *v, const int64_t *t, uint64_t m,
+                            uint32_t n, uint64_t *S, uint64_t width, int reverse)
 {
     if (m == 0)
         return TNREF_OK;
     int rc = tnref_validate(u, v, t, m, n);
     if (rc != TNREF_OK)
         return rc;
-
-    int64_t *slot = (int64_t *)malloc((size_t)n * sizeof(int64_t));
-    uint32_t *touched = NULL;
-    uint64_t *old = NULL;
-    uint64_t cap = 0;
-    if (!slot)
+    struct tnref_groups gs = {NULL, NULL, NULL, 0};
+    gs.slot = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    if (!gs.slot)
         return TNREF_ENOMEM;
     for (uint32_t i = 0; i < n; ++i)
-        slot[i] = -1;
-
-    uint64_t g0 = 0;
-    while (g0 < m) {
-        uint64_t g1 = g0 + 1;
-        while (g1 < m && t[g1] == t[g0])
-            ++g1;
-        uint64_t need = 2 * (g1 - g0);
-        if (need > cap) {
-            free(touched);
-            free(old);
-            cap = need;
-            touched = (uint32_t *)malloc(cap * sizeof(uint32_t));
-            old = (uint64_t *)malloc(cap * width * sizeof(uint64_t));
-            if (!touched || !old) {
-                free(slot);
-                free(touched);
-                free(old);
-                return TNREF_ENOMEM;
-            }
+        gs.slot[i] = -1;
+    if (!reverse) {
+        uint64_t g0 = 0;
+        while (g0 < m && rc == TNREF_OK) {
+            uint64_t g1 = g0 + 1;
+            while (g1 < m && t[g1] == t[g0])
+                ++g1;
+            rc = apply_group(&gs, u, v, g0, g1, S, width);
+            g0 = g1;
         }
-        /* snapshot the rows of the group's nodes */
-        uint64_t nt = 0;
-        for (uint64_t e = g0; e < g1; ++e) {
-            uint32_t ends[2] = {u[e], v[e]};
-            for (int q = 0; q < 2; ++q) {
-                uint32_t x = ends[q];
-                if (slot[x] < 0) {
-                    slot[x] = (int64_t)nt;
-                    touched[nt] = x;
-                    memcpy(old + nt * width, S + (uint64_t)x * width,
-                           width * sizeof(uint64_t));
-                    ++nt;
-                }
-            }
+    } else {
+        uint64_t g1 = m;
+        while (g1 > 0 && rc == TNREF_OK) {
+            uint64_t g0 = g1 - 1;
+            while (g0 > 0 && t[g0 - 1] == t[g1 - 1])
+                --g0;
+            rc = apply_group(&gs, u, v, g0, g1, S, width);
+            g1 = g0;
         }
-        /* OR the partners' old rows into each endpoint */
-        for (uint64_t e = g0; e < g1; ++e) {
-            uint64_t *ra = S + (uint64_t)u[e] * width;
-            uint64_t *rb = S + (uint64_t)v[e] * width;
-            const uint64_t *oa = old + (uint64_t)slot[u[e]] * width;
-            const uint64_t *ob = old + (uint64_t)slot[v[e]] * width;
-            for (uint64_t w = 0; w < width; ++w) {
-                ra[w] |= ob[w];
-                rb[w] |= oa[w];
-            }
-        }
-        for (uint64_t k = 0; k < nt; ++k)
-            slot[touched[k]] = -1;
-        g0 = g1;
     }
-    free(slot);
-    free(touched);
-    free(old);
-    return TNREF_OK;
+    free(gs.slot);
+    free(gs.touched);
+    free(gs.old);
+    return rc;
+}
+
+int tnref_apply_events(const uint32_t *u, const uint32_t *v, const int64_t *t,
+                       uint64_t m, uint32_t n, uint64_t *S, uint64_t width)
+{
+    return apply_events_dir(u, v, t, m, n, S, width, 0);
+}
+
+int tnref_apply_events_reversed(const uint32_t *u, const uint32_t *v, const int64_t *t,
+                                uint64_t m, uint32_t n, uint64_t *S, uint64_t width)
+{
+    return apply_events_dir(u, v, t, m, n, S, width, 1);
 }
 
 /* ---------------------------------------------------------------------------

@@ -417,3 +417,37 @@ def test_error_stats_w1_is_emd():
 def test_error_stats_rejects_zero_exact_size():
     with pytest.raises(Exception):
         oracle.error_stats([1, 2], [1, 0])
+
+
+# --------------------------------------------------------------------------
+# reversed-sequence variant (Section 3.4)
+# --------------------------------------------------------------------------
+def test_reversed_hand_example():
+    # 0-1 at t=1, 1-2 at t=2: forward, 0 reaches 1 and 2, 1 reaches 0 (t=1) and 2 (t=2), 2 reaches 1 only
+    u = np.array([0, 1], np.uint32); v = np.array([1, 2], np.uint32); t = np.array([1, 2], np.int64)
+    R = oracle.to_bool(oracle.component_matrix_reversed(u, v, t, 3), 3)
+    assert R.tolist() == [[True, True, True], [True, True, True], [False, True, True]]
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_reversed_is_transpose_of_forward(seed):
+    """Reversing time turns in-components into out-components: row i of the
+    reversed result is column i of the forward matrix (ties stay snapshots in
+    both directions, so the relation is exact)."""
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(2, 90))
+    m = int(rng.integers(1, 400))
+    u, v, t = synth.uniform_events(n, m, t_range=int(rng.integers(1, 60)), seed=seed, self_loops=True)
+    F = oracle.to_bool(oracle.component_matrix(u, v, t, n), n)
+    R = oracle.to_bool(oracle.component_matrix_reversed(u, v, t, n), n)
+    assert np.array_equal(R, F.T)
+
+
+def test_reversed_rows_match_brute_force_si():
+    """Row i of the reversed result is the set the SI process from i infects."""
+    rng = np.random.default_rng(77)
+    n, m = 40, 300
+    u, v, t = synth.uniform_events(n, m, t_range=50, seed=77)
+    R = oracle.to_bool(oracle.component_matrix_reversed(u, v, t, n), n)
+    for i in rng.choice(n, 10, replace=False):
+        assert np.array_equal(R[i], oracle.si_reach(u, v, t, n, int(i)).astype(bool))
