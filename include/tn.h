@@ -76,6 +76,12 @@ typedef int32_t tn_status;
 
 /* Flags of tn_component_matrix / tn_component_columns / tn_plan_apply. */
 #define TN_INIT_IDENTITY 1u /* initialise S first: identity, or the source columns */
+#define TN_REVERSE 2u       /* tn_component_matrix / tn_component_columns only: process
+                               the sequence from its last timestamp group to its first
+                               (Section 3.4); row i then ends as the OUT-component of i,
+                               i.e. the result is the transpose of the chronological
+                               matrix.  Requires TN_INIT_IDENTITY and t_last == NULL
+                               (it is not a streaming mode).  Scratch: 16 bytes per event. */
 
 /* Human-readable name of a status code (static storage, never NULL). */
 const char *tn_status_string(tn_status status);

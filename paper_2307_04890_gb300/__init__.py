@@ -25,12 +25,13 @@ __all__ = [
     "tn_out_component_sizes_host",
     "Plan", "tn_plan_apply_batch", "Server", "BatchGraph", "tn_autotune",
     "TN_OK", "TN_EINVAL", "TN_ERANGE", "TN_EORDER", "TN_ENOMEM", "TN_ECUDA", "TN_ETIMEOUT", "TN_ESCRATCH",
-    "TN_INIT_IDENTITY",
+    "TN_INIT_IDENTITY", "TN_REVERSE",
 ]
 
 TN_OK, TN_EINVAL, TN_ERANGE, TN_EORDER, TN_ENOMEM, TN_ECUDA, TN_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 TN_ESCRATCH = -7
 TN_INIT_IDENTITY = 1
+TN_REVERSE = 2
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIBRARY_PATH = os.path.join(_HERE, "libtn.so")
@@ -212,27 +213,33 @@ def _matrix(S, n_rows, ncols, device):
     return S
 
 
-def tn_component_matrix(u, v, t, n: int, S=None, t_last=None, init: bool = True, stream=None):
-    """Algorithm 1 (Section 3.1) over one event batch; returns S (int64 [n, W])."""
+def tn_component_matrix(u, v, t, n: int, S=None, t_last=None, init: bool = True, reverse: bool = False,
+                        stream=None):
+    """Algorithm 1 (Section 3.1) over one event batch; returns S (int64 [n, W]).
+    reverse=True processes the sequence backwards (Section 3.4): row i is then
+    the out-component of i (the transpose of the chronological matrix)."""
     lib = load_library()
     m = _events(u, v, t)
     S = _matrix(S, n, n, u.device)
     if t_last is not None:
         _dev(t_last, ("int64",), "t_last")
-    _check(lib.tn_component_matrix(_ptr(u), _ptr(v), _ptr(t), m, n, _ptr(S), _ptr(t_last),
-                                   TN_INIT_IDENTITY if init else 0, _stream(stream)), "tn_component_matrix")
+    flags = (TN_INIT_IDENTITY if init else 0) | (TN_REVERSE if reverse else 0)
+    _check(lib.tn_component_matrix(_ptr(u), _ptr(v), _ptr(t), m, n, _ptr(S), _ptr(t_last), flags,
+                                   _stream(stream)), "tn_component_matrix")
     return S
 
 
-def tn_component_columns(u, v, t, n: int, src, S=None, t_last=None, init: bool = True, stream=None):
-    """Out-components of the listed sources only (column c = source src[c])."""
+def tn_component_columns(u, v, t, n: int, src, S=None, t_last=None, init: bool = True, reverse: bool = False,
+                         stream=None):
+    """Out-components of the listed sources only (column c = source src[c]);
+    with reverse=True, column c is the in-component of src[c]."""
     lib = load_library()
     m = _events(u, v, t)
     _dev(src, ("int32", "uint32"), "src")
     S = _matrix(S, n, src.numel(), u.device)
+    flags = (TN_INIT_IDENTITY if init else 0) | (TN_REVERSE if reverse else 0)
     _check(lib.tn_component_columns(_ptr(u), _ptr(v), _ptr(t), m, n, _ptr(src), src.numel(), _ptr(S),
-                                    _ptr(t_last), TN_INIT_IDENTITY if init else 0, _stream(stream)),
-           "tn_component_columns")
+                                    _ptr(t_last), flags, _stream(stream)), "tn_component_columns")
     return S
 
 

@@ -622,11 +622,53 @@ extern "C" tn_status tn_plan_apply_batch(const tn_plan *const *plans, uint64_t *
     return rc;
 }
 
+// reversed sequence (Section 3.4): event m-1-e becomes event e and its time is
+// complemented (~t = -t - 1 keeps equal times equal and the order non-decreasing)
+__global__ void reverse_events_kernel(const uint32_t *u, const uint32_t *v, const int64_t *t, uint64_t m,
+                                      uint32_t *ru, uint32_t *rv, int64_t *rt)
+{
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < m; e += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t s = m - 1 - e;
+        ru[e] = u[s];
+        rv[e] = v[s];
+        rt[e] = ~t[s];
+    }
+}
+
+static tn_status one_shot(const uint32_t *u, const uint32_t *v, const int64_t *t, uint64_t m, uint32_t n,
+                          const uint32_t *src, uint32_t ncols, uint64_t *S, int64_t *t_last, uint32_t flags,
+                          void *stream);
+
+// TN_REVERSE: the same path over the reversed sequence, from the identity
+static tn_status one_shot_reversed(const uint32_t *u, const uint32_t *v, const int64_t *t, uint64_t m, uint32_t n,
+                                   const uint32_t *src, uint32_t ncols, uint64_t *S, int64_t *t_last,
+                                   uint32_t flags, void *stream)
+{
+    if (t_last || !(flags & TN_INIT_IDENTITY)) return TN_EINVAL;  // not a streaming mode
+    if (m == 0) return one_shot(u, v, t, m, n, src, ncols, S, nullptr, flags & ~TN_REVERSE, stream);
+    if (!u || !v || !t || m >= (1ull << 30)) return TN_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    uint32_t *ru = nullptr, *rv = nullptr;
+    int64_t *rt = nullptr;
+    TN_CUDA_TRY(cudaMallocAsync((void **)&ru, m * 4, st));
+    TN_CUDA_TRY(cudaMallocAsync((void **)&rv, m * 4, st));
+    TN_CUDA_TRY(cudaMallocAsync((void **)&rt, m * 8, st));
+    tn_internal_count_launches(1);
+    reverse_events_kernel<<<grid_for(m), 256, 0, st>>>(u, v, t, m, ru, rv, rt);
+    TN_CUDA_TRY(cudaGetLastError());
+    const tn_status rc = one_shot(ru, rv, rt, m, n, src, ncols, S, nullptr, flags & ~TN_REVERSE, stream);
+    cudaFreeAsync(ru, st);
+    cudaFreeAsync(rv, st);
+    cudaFreeAsync(rt, st);
+    return rc;
+}
+
 static tn_status one_shot(const uint32_t *u, const uint32_t *v, const int64_t *t, uint64_t m, uint32_t n,
                           const uint32_t *src, uint32_t ncols, uint64_t *S, int64_t *t_last, uint32_t flags,
                           void *stream)
 {
-    if (!S || n == 0 || n >= (1u << 30) || (flags & ~TN_INIT_IDENTITY)) return TN_EINVAL;
+    if (!S || n == 0 || n >= (1u << 30) || (flags & ~(TN_INIT_IDENTITY | TN_REVERSE))) return TN_EINVAL;
+    if (flags & TN_REVERSE) return one_shot_reversed(u, v, t, m, n, src, ncols, S, t_last, flags, stream);
     cudaStream_t st = (cudaStream_t)stream;
     const uint64_t ld = tn_row_words(ncols);
     if (src && (flags & TN_INIT_IDENTITY)) {

@@ -437,3 +437,33 @@ def test_estimate_bitsliced_chunks_and_both_paths_agree():
     small = torch.zeros(len(sample), dtype=torch.int32, device="cuda")
     tn.tn_hash_estimate_noalloc(P, R, k, H, n, small, src=few)  # byte-table fusion
     assert np.array_equal(u32(small), est[sample])
+
+
+# --------------------------------------------------------------------------
+# reversed sequence (Section 3.4)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("n,m,t_range,seed", [(300, 5000, 800, 1), (1500, 40_000, 30, 2), (70, 3000, 4000, 3)])
+def test_reversed_matrix_is_transposed(n, m, t_range, seed):
+    u, v, t = synth.uniform_events(n, m, t_range=t_range, seed=seed, self_loops=True)
+    du, dv, dt = dev_events(u, v, t)
+    R = tn.tn_component_matrix(du, dv, dt, n, reverse=True)
+    torch.cuda.synchronize()
+    got = host_matrix(R, n)
+    assert np.array_equal(got, oracle.component_matrix_reversed(u, v, t, n))
+    F = oracle.to_bool(oracle.component_matrix(u, v, t, n), n)
+    assert np.array_equal(oracle.to_bool(got, n), F.T)
+    # in-sizes of the reversed matrix are the out-sizes of the chronological one
+    _, ins, _ = tn.tn_out_sizes(R, n, n, in_sizes=True)
+    assert np.array_equal(u32(ins), oracle.column_counts(oracle.component_matrix(u, v, t, n), n))
+
+
+def test_reversed_rejects_streaming_use():
+    n = 50
+    u, v, t = synth.uniform_events(n, 200, t_range=100, seed=4)
+    du, dv, dt = dev_events(u, v, t)
+    t_last = torch.full((1,), -1, dtype=torch.int64, device="cuda")
+    with pytest.raises(tn.TnError) as exc:
+        tn.tn_component_matrix(du, dv, dt, n, t_last=t_last, reverse=True)
+    assert exc.value.status == tn.TN_EINVAL
+    with pytest.raises(tn.TnError):
+        tn.tn_component_matrix(du, dv, dt, n, init=False, reverse=True)
