@@ -10,6 +10,8 @@ arrays.  Functions cite the paper passage they follow:
 * ``component_matrix``  -- Algorithm 1 (Section 3.1) with equal-timestamp
   groups applied as snapshots (adjacency needs dt > 0, Section 2.1).
 * ``component_matrix_reversed`` -- the reversed-sequence variant (Section 3.4).
+* ``component_matrix_directed`` / ``si_reach_directed`` -- directed events
+  (footnote to Section 3.1: only the receiver's row is updated).
 * ``si_reach``          -- the deterministic SI process (Section 1).
 * ``column_counts`` / ``row_counts`` / ``argmax`` -- component sizes
   (Section 3.1, eq. for the mean size s_t in Section 3.3).
@@ -68,6 +70,11 @@ def _load():
         lib.tnref_apply_events.restype = ctypes.c_int
         lib.tnref_apply_events_reversed.argtypes = lib.tnref_apply_events.argtypes
         lib.tnref_apply_events_reversed.restype = ctypes.c_int
+        lib.tnref_apply_events_directed.argtypes = lib.tnref_apply_events.argtypes
+        lib.tnref_apply_events_directed.restype = ctypes.c_int
+        lib.tnref_si_reach_directed.argtypes = [_u32p, _u32p, _i64p, ctypes.c_uint64, ctypes.c_uint32,
+                                                ctypes.c_uint32, _u8p]
+        lib.tnref_si_reach_directed.restype = ctypes.c_int
         lib.tnref_si_reach.argtypes = [_u32p, _u32p, _i64p, ctypes.c_uint64, ctypes.c_uint32,
                                        ctypes.c_uint32, _u8p]
         lib.tnref_si_reach.restype = ctypes.c_int
@@ -158,6 +165,23 @@ def component_matrix_reversed(u, v, t, n) -> np.ndarray:
     S = init_sources(n)
     _check(_load().tnref_apply_events_reversed(u, v, t, len(u), n, S.reshape(-1), S.shape[1]))
     return S
+
+
+def component_matrix_directed(u, v, t, n, src=None) -> np.ndarray:
+    """Directed events (footnote to Section 3.1): S[v] |= S[u] only, timestamp
+    groups as snapshots; from the identity (or the listed source columns)."""
+    u, v, t = _ev(u, v, t)
+    S = init_sources(n, src)
+    _check(_load().tnref_apply_events_directed(u, v, t, len(u), n, S.reshape(-1), S.shape[1]))
+    return S
+
+
+def si_reach_directed(u, v, t, n, source) -> np.ndarray:
+    """Deterministic SI process over directed events from one source; bool[n]."""
+    u, v, t = _ev(u, v, t)
+    out = np.zeros(n, dtype=np.uint8)
+    _check(_load().tnref_si_reach_directed(u, v, t, len(u), n, source, out))
+    return out.astype(bool)
 
 
 def si_reach(u, v, t, n, source) -> np.ndarray:

@@ -181,6 +181,72 @@ static int apply_events_dir(const uint32_t *u, const uint32_t *v, const int64_t 
     return rc;
 }
 
+/* Directed events (the paper's footnote to Section 3.1: only the receiving
+ * node's row is updated, S[v] |= S[u]).  One timestamp group [g0, g1) is a
+ * snapshot: S_new[v] = S_old[v] OR (OR over events u -> v of the group of
+ * S_old[u]); the sources' old rows are copied first. */
+static int apply_group_directed(struct tnref_groups *gs, const uint32_t *u, const uint32_t *v, uint64_t g0,
+                                uint64_t g1, uint64_t *S, uint64_t width)
+{
+    uint64_t need = g1 - g0;
+    if (need > gs->cap) {
+        free(gs->touched);
+        free(gs->old);
+        gs->cap = need;
+        gs->touched = (uint32_t *)malloc(gs->cap * sizeof(uint32_t));
+        gs->old = (uint64_t *)malloc(gs->cap * width * sizeof(uint64_t));
+        if (!gs->touched || !gs->old)
+            return TNREF_ENOMEM;
+    }
+    uint64_t nt = 0;
+    for (uint64_t e = g0; e < g1; ++e) {
+        uint32_t x = u[e];
+        if (gs->slot[x] < 0) {
+            gs->slot[x] = (int64_t)nt;
+            gs->touched[nt] = x;
+            memcpy(gs->old + nt * width, S + (uint64_t)x * width, width * sizeof(uint64_t));
+            ++nt;
+        }
+    }
+    for (uint64_t e = g0; e < g1; ++e) {
+        uint64_t *rv = S + (uint64_t)v[e] * width;
+        const uint64_t *ou = gs->old + (uint64_t)gs->slot[u[e]] * width;
+        for (uint64_t w = 0; w < width; ++w)
+            rv[w] |= ou[w];
+    }
+    for (uint64_t k = 0; k < nt; ++k)
+        gs->slot[gs->touched[k]] = -1;
+    return TNREF_OK;
+}
+
+int tnref_apply_events_directed(const uint32_t *u, const uint32_t *v, const int64_t *t,
+                                uint64_t m, uint32_t n, uint64_t *S, uint64_t width)
+{
+    if (m == 0)
+        return TNREF_OK;
+    int rc = tnref_validate(u, v, t, m, n);
+    if (rc != TNREF_OK)
+        return rc;
+    struct tnref_groups gs = {NULL, NULL, NULL, 0};
+    gs.slot = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    if (!gs.slot)
+        return TNREF_ENOMEM;
+    for (uint32_t i = 0; i < n; ++i)
+        gs.slot[i] = -1;
+    uint64_t g0 = 0;
+    while (g0 < m && rc == TNREF_OK) {
+        uint64_t g1 = g0 + 1;
+        while (g1 < m && t[g1] == t[g0])
+            ++g1;
+        rc = apply_group_directed(&gs, u, v, g0, g1, S, width);
+        g0 = g1;
+    }
+    free(gs.slot);
+    free(gs.touched);
+    free(gs.old);
+    return rc;
+}
+
 int tnref_apply_events(const uint32_t *u, const uint32_t *v, const int64_t *t,
                        uint64_t m, uint32_t n, uint64_t *S, uint64_t width)
 {
@@ -451,5 +517,40 @@ int tnref_error_stats(const uint32_t *a, const uint32_t *b, uint64_t count,
     *w1_num = w;
     *rel_sum = rs;
     *max_rel = mr;
+    return TNREF_OK;
+}
+
+/* Deterministic SI over directed events: an infected u infects v at the
+ * event's time (infections of one timestamp are decided on the state before
+ * it). */
+int tnref_si_reach_directed(const uint32_t *u, const uint32_t *v, const int64_t *t,
+                            uint64_t m, uint32_t n, uint32_t source, uint8_t *reached)
+{
+    if (source >= n)
+        return TNREF_EINVAL;
+    int rc = tnref_validate(u, v, t, m, n);
+    if (rc != TNREF_OK)
+        return rc;
+    memset(reached, 0, n);
+    reached[source] = 1;
+    uint8_t *fresh = (uint8_t *)calloc(n, 1);
+    if (!fresh)
+        return TNREF_ENOMEM;
+    uint64_t g0 = 0;
+    while (g0 < m) {
+        uint64_t g1 = g0 + 1;
+        while (g1 < m && t[g1] == t[g0])
+            ++g1;
+        for (uint64_t e = g0; e < g1; ++e)
+            if (reached[u[e]])
+                fresh[v[e]] = 1;
+        for (uint64_t e = g0; e < g1; ++e)
+            if (fresh[v[e]]) {
+                reached[v[e]] = 1;
+                fresh[v[e]] = 0;
+            }
+        g0 = g1;
+    }
+    free(fresh);
     return TNREF_OK;
 }

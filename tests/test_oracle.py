@@ -451,3 +451,56 @@ def test_reversed_rows_match_brute_force_si():
     R = oracle.to_bool(oracle.component_matrix_reversed(u, v, t, n), n)
     for i in rng.choice(n, 10, replace=False):
         assert np.array_equal(R[i], oracle.si_reach(u, v, t, n, int(i)).astype(bool))
+
+
+# --------------------------------------------------------------------------
+# directed events (footnote to Section 3.1: S[v] |= S[u] only)
+# --------------------------------------------------------------------------
+def test_directed_hand_example():
+    # 0->1 at t=1, 1->2 at t=2, 2->0 at t=2: 0 reaches 1 and 2; 1 reaches 2; 2 reaches 0 only;
+    # 1 -> 2 and 2 -> 0 share t=2, so 1 does not reach 0 through 2
+    u = np.array([0, 1, 2], np.uint32); v = np.array([1, 2, 0], np.uint32); t = np.array([1, 2, 2], np.int64)
+    B = oracle.to_bool(oracle.component_matrix_directed(u, v, t, 3), 3)  # B[i, j]: i reached from j
+    assert B[:, 0].tolist() == [True, True, True]
+    assert B[:, 1].tolist() == [False, True, True]
+    assert B[:, 2].tolist() == [True, False, True]
+
+
+@pytest.mark.parametrize("seed", range(20))
+def test_directed_matches_directed_si(seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(2, 40))
+    m = int(rng.integers(1, 200))
+    u, v, t = synth.uniform_events(n, m, t_range=int(rng.integers(1, 30)), seed=seed, self_loops=True)
+    B = oracle.to_bool(oracle.component_matrix_directed(u, v, t, n), n)
+    for j in range(n):
+        assert np.array_equal(B[:, j], oracle.si_reach_directed(u, v, t, n, j)), j
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_undirected_is_both_directions_at_once(seed):
+    """An undirected event is the two directed events u->v and v->u at the
+    same timestamp (one snapshot), so the directed rule on the doubled stream
+    must give the undirected matrix."""
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.integers(2, 120))
+    m = int(rng.integers(1, 500))
+    u, v, t = synth.uniform_events(n, m, t_range=int(rng.integers(1, 80)), seed=seed, self_loops=True)
+    du = np.stack([u, v], 1).reshape(-1)
+    dv = np.stack([v, u], 1).reshape(-1)
+    dt = np.repeat(t, 2)
+    assert np.array_equal(oracle.component_matrix_directed(du, dv, dt, n), oracle.component_matrix(u, v, t, n))
+
+
+def test_directed_exhaustive_tiny():
+    """Every directed sequence of up to 3 events on 3 nodes over 2 timestamps."""
+    pairs = [(a, b) for a in range(3) for b in range(3)]
+    for k in range(1, 4):
+        for evs in itertools.product(pairs, repeat=k):
+            for ts in itertools.product(range(2), repeat=k):
+                t = np.sort(np.array(ts, np.int64))
+                u = np.array([e[0] for e in evs], np.uint32)
+                v = np.array([e[1] for e in evs], np.uint32)
+                B = oracle.to_bool(oracle.component_matrix_directed(u, v, t, 3), 3)
+                for j in range(3):
+                    assert np.array_equal(B[:, j], oracle.si_reach_directed(u, v, t, 3, j))
