@@ -76,11 +76,15 @@ typedef int32_t tn_status;
 
 /* Flags of tn_component_matrix / tn_component_columns / tn_plan_apply. */
 #define TN_INIT_IDENTITY 1u /* initialise S first: identity, or the source columns */
+#define TN_DIRECTED 4u      /* tn_component_matrix / tn_component_columns only: events
+                               are directed u -> v (see tn_plan_options.directed) */
 #define TN_REVERSE 2u       /* tn_component_matrix / tn_component_columns only: process
                                the sequence from its last timestamp group to its first
                                (Section 3.4); row i then ends as the OUT-component of i,
                                i.e. the result is the transpose of the chronological
-                               matrix.  Requires TN_INIT_IDENTITY and t_last == NULL
+                               matrix (with TN_DIRECTED the events are also turned
+                               around, v -> u, so this still holds).  Requires
+                               TN_INIT_IDENTITY and t_last == NULL
                                (it is not a streaming mode).  Scratch: 16 bytes per event. */
 
 /* Human-readable name of a status code (static storage, never NULL). */
@@ -183,7 +187,10 @@ typedef struct tn_plan_options {
                                buffer (at most 160 KB / (8 slab_words)); windows with
                                more rows (plus saved copies) stream from global
                                memory (0 = 160 KB / (8 slab_words)) */
-    uint32_t reserved[5];   /* must be zero */
+    uint32_t directed;      /* 1: event (u, v, t) is directed u -> v and only S[v] is
+                               updated, S[v] |= S[u] (the paper's footnote to Section
+                               3.1); timestamp groups stay snapshots.  0: undirected */
+    uint32_t reserved[4];   /* must be zero */
 } tn_plan_options;
 
 typedef struct tn_plan_stats {
@@ -441,6 +448,16 @@ tn_status tn_server_get_stats(tn_server *server, tn_server_stats *stats);
 /* Finishes every queued and running job, then stops the worker and frees the
  * server (records not yet polled are dropped). */
 tn_status tn_server_destroy(tn_server *server);
+
+/* ---------------------------------------------------------------------------
+ * tn_selftest_wait_timeout -- exercises the bounded device waits that every
+ * kernel of this library uses instead of unbounded spins: a kernel waits on a
+ * barrier that nothing completes and gives up after its poll limit (a few
+ * seconds at most).  Returns TN_ETIMEOUT when the bounded wait works (the
+ * context stays usable), TN_OK never.  Synchronous.  No counterpart in the
+ * paper: it checks this library's failure handling.
+ */
+tn_status tn_selftest_wait_timeout(void *stream);
 
 /* ---------------------------------------------------------------------------
  * tn_out_component_sizes_host -- the whole exact path from HOST arrays:

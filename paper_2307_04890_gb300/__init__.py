@@ -23,15 +23,16 @@ __all__ = [
     "tn_component_matrix", "tn_component_columns", "tn_out_sizes",
     "tn_hash_proxy", "tn_hash_estimate", "tn_hash_estimate_noalloc", "tn_error_stats",
     "tn_out_component_sizes_host",
-    "Plan", "tn_plan_apply_batch", "Server", "BatchGraph", "tn_autotune",
+    "Plan", "tn_plan_apply_batch", "Server", "BatchGraph", "tn_autotune", "tn_selftest_wait_timeout",
     "TN_OK", "TN_EINVAL", "TN_ERANGE", "TN_EORDER", "TN_ENOMEM", "TN_ECUDA", "TN_ETIMEOUT", "TN_ESCRATCH",
-    "TN_INIT_IDENTITY", "TN_REVERSE",
+    "TN_INIT_IDENTITY", "TN_REVERSE", "TN_DIRECTED",
 ]
 
 TN_OK, TN_EINVAL, TN_ERANGE, TN_EORDER, TN_ENOMEM, TN_ECUDA, TN_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 TN_ESCRATCH = -7
 TN_INIT_IDENTITY = 1
 TN_REVERSE = 2
+TN_DIRECTED = 4
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIBRARY_PATH = os.path.join(_HERE, "libtn.so")
@@ -53,7 +54,7 @@ class TnError(RuntimeError):
 
 class _Options(ctypes.Structure):
     _fields_ = [("window_events", ctypes.c_uint32), ("slab_words", ctypes.c_uint32),
-                ("smem_rows", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 5)]
+                ("smem_rows", ctypes.c_uint32), ("directed", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 4)]
 
 
 class _ErrorStats(ctypes.Structure):
@@ -125,6 +126,7 @@ def load_library(path: str | None = None):
         "tn_graph_launch": ([vp, vp], i32),
         "tn_graph_destroy": ([vp], i32),
         "tn_autotune": ([vp, vp, vp, u64, u32, u32, u32, u64, vp, ctypes.POINTER(_TuneResult)], i32),
+        "tn_selftest_wait_timeout": ([vp], i32),
         "tn_server_create": ([ctypes.POINTER(_ServerOptions), ctypes.POINTER(vp)], i32),
         "tn_server_submit": ([vp, u64, u32, vp, vp, vp, vp, u32, vp, vp], i32),
         "tn_server_poll": ([vp, ctypes.POINTER(_JobRecord), u32, ctypes.POINTER(u32), u32], i32),
@@ -214,7 +216,7 @@ def _matrix(S, n_rows, ncols, device):
 
 
 def tn_component_matrix(u, v, t, n: int, S=None, t_last=None, init: bool = True, reverse: bool = False,
-                        stream=None):
+                        directed: bool = False, stream=None):
     """Algorithm 1 (Section 3.1) over one event batch; returns S (int64 [n, W]).
     reverse=True processes the sequence backwards (Section 3.4): row i is then
     the out-component of i (the transpose of the chronological matrix)."""
@@ -223,21 +225,21 @@ def tn_component_matrix(u, v, t, n: int, S=None, t_last=None, init: bool = True,
     S = _matrix(S, n, n, u.device)
     if t_last is not None:
         _dev(t_last, ("int64",), "t_last")
-    flags = (TN_INIT_IDENTITY if init else 0) | (TN_REVERSE if reverse else 0)
+    flags = (TN_INIT_IDENTITY if init else 0) | (TN_REVERSE if reverse else 0) | (TN_DIRECTED if directed else 0)
     _check(lib.tn_component_matrix(_ptr(u), _ptr(v), _ptr(t), m, n, _ptr(S), _ptr(t_last), flags,
                                    _stream(stream)), "tn_component_matrix")
     return S
 
 
 def tn_component_columns(u, v, t, n: int, src, S=None, t_last=None, init: bool = True, reverse: bool = False,
-                         stream=None):
+                         directed: bool = False, stream=None):
     """Out-components of the listed sources only (column c = source src[c]);
     with reverse=True, column c is the in-component of src[c]."""
     lib = load_library()
     m = _events(u, v, t)
     _dev(src, ("int32", "uint32"), "src")
     S = _matrix(S, n, src.numel(), u.device)
-    flags = (TN_INIT_IDENTITY if init else 0) | (TN_REVERSE if reverse else 0)
+    flags = (TN_INIT_IDENTITY if init else 0) | (TN_REVERSE if reverse else 0) | (TN_DIRECTED if directed else 0)
     _check(lib.tn_component_columns(_ptr(u), _ptr(v), _ptr(t), m, n, _ptr(src), src.numel(), _ptr(S),
                                     _ptr(t_last), flags, _stream(stream)), "tn_component_columns")
     return S
@@ -349,12 +351,12 @@ class Plan:
     """A validated, scheduled event batch (tn_plan_create / tn_plan_apply)."""
 
     def __init__(self, u, v, t, n: int, t_after=None, window_events: int = 0, slab_words: int = 0,
-                 smem_rows: int = 0, stream=None):
+                 smem_rows: int = 0, directed: bool = False, stream=None):
         lib = load_library()
         self.m = _events(u, v, t)
         self.n = n
         self.device = u.device
-        opt = _Options(window_events, slab_words, smem_rows)
+        opt = _Options(window_events, slab_words, smem_rows, 1 if directed else 0)
         h = ctypes.c_void_p()
         if t_after is not None:
             _dev(t_after, ("int64",), "t_after")
@@ -520,3 +522,8 @@ class BatchGraph:
             self.destroy()
         except Exception:
             pass
+
+
+def tn_selftest_wait_timeout(stream=None) -> int:
+    """Runs the bounded-wait self-test; returns its status (TN_ETIMEOUT expected)."""
+    return int(load_library().tn_selftest_wait_timeout(_stream(stream)))

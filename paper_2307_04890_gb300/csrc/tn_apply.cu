@@ -441,6 +441,18 @@ __global__ void __launch_bounds__(kThreads) stream_kernel(const __grid_constant_
     }
 }
 
+// Self-test of the bounded waits: one thread waits on an mbarrier that nothing
+// ever completes, through the same bounded wait the streaming kernel uses, and
+// records TN_ETIMEOUT when the wait gives up.
+__global__ void wait_selftest_kernel(int32_t *status)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    if (!mbar_wait_bounded(&bar, 0)) record_status(status, TN_ETIMEOUT);
+}
+
 // S <- identity (full matrix) -- Algorithm 1, first line; one row per warp step
 __global__ void init_identity_kernel(uint64_t *S, uint32_t n_rows, uint64_t ld, const int32_t *status)
 {
@@ -624,13 +636,15 @@ extern "C" tn_status tn_plan_apply_batch(const tn_plan *const *plans, uint64_t *
 
 // reversed sequence (Section 3.4): event m-1-e becomes event e and its time is
 // complemented (~t = -t - 1 keeps equal times equal and the order non-decreasing)
+// Directed events are also turned around (u -> v becomes v -> u), so that in
+// both modes row i ends as the out-component of i.
 __global__ void reverse_events_kernel(const uint32_t *u, const uint32_t *v, const int64_t *t, uint64_t m,
-                                      uint32_t *ru, uint32_t *rv, int64_t *rt)
+                                      bool turn, uint32_t *ru, uint32_t *rv, int64_t *rt)
 {
     for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < m; e += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t s = m - 1 - e;
-        ru[e] = u[s];
-        rv[e] = v[s];
+        ru[e] = turn ? v[s] : u[s];
+        rv[e] = turn ? u[s] : v[s];
         rt[e] = ~t[s];
     }
 }
@@ -654,7 +668,7 @@ static tn_status one_shot_reversed(const uint32_t *u, const uint32_t *v, const i
     TN_CUDA_TRY(cudaMallocAsync((void **)&rv, m * 4, st));
     TN_CUDA_TRY(cudaMallocAsync((void **)&rt, m * 8, st));
     tn_internal_count_launches(1);
-    reverse_events_kernel<<<grid_for(m), 256, 0, st>>>(u, v, t, m, ru, rv, rt);
+    reverse_events_kernel<<<grid_for(m), 256, 0, st>>>(u, v, t, m, (flags & TN_DIRECTED) != 0, ru, rv, rt);
     TN_CUDA_TRY(cudaGetLastError());
     const tn_status rc = one_shot(ru, rv, rt, m, n, src, ncols, S, nullptr, flags & ~TN_REVERSE, stream);
     cudaFreeAsync(ru, st);
@@ -667,7 +681,7 @@ static tn_status one_shot(const uint32_t *u, const uint32_t *v, const int64_t *t
                           const uint32_t *src, uint32_t ncols, uint64_t *S, int64_t *t_last, uint32_t flags,
                           void *stream)
 {
-    if (!S || n == 0 || n >= (1u << 30) || (flags & ~(TN_INIT_IDENTITY | TN_REVERSE))) return TN_EINVAL;
+    if (!S || n == 0 || n >= (1u << 30) || (flags & ~(TN_INIT_IDENTITY | TN_REVERSE | TN_DIRECTED))) return TN_EINVAL;
     if (flags & TN_REVERSE) return one_shot_reversed(u, v, t, m, n, src, ncols, S, t_last, flags, stream);
     cudaStream_t st = (cudaStream_t)stream;
     const uint64_t ld = tn_row_words(ncols);
@@ -694,9 +708,13 @@ static tn_status one_shot(const uint32_t *u, const uint32_t *v, const int64_t *t
         }
         return TN_OK;
     }
+    tn_plan_options opt;
+    memset(&opt, 0, sizeof(opt));
+    opt.directed = (flags & TN_DIRECTED) ? 1u : 0u;
     tn_plan *plan = nullptr;
-    tn_status rc = tn_plan_create(u, v, t, m, n, t_last, nullptr, stream, &plan);
+    tn_status rc = tn_plan_create(u, v, t, m, n, t_last, &opt, stream, &plan);
     if (rc != TN_OK) return rc;
+    flags &= ~TN_DIRECTED;
     rc = apply_jobs((const tn_plan *const *)&plan, &S, &ncols, &src, &t_last, 1, flags, st);
     tn_plan_destroy(plan, stream);
     return rc;
@@ -740,4 +758,19 @@ extern "C" tn_status tn_init_matrix(uint64_t *S, uint32_t n_rows, uint32_t ncols
     TN_CUDA_TRY(cudaGetLastError());
     TN_CUDA_TRY(cudaFreeAsync(zero, st));
     return TN_OK;
+}
+
+extern "C" tn_status tn_selftest_wait_timeout(void *stream)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    int32_t *d = nullptr, h = 0;
+    TN_CUDA_TRY(cudaMallocAsync((void **)&d, sizeof(int32_t), st));
+    TN_CUDA_TRY(cudaMemsetAsync(d, 0, sizeof(int32_t), st));
+    tn_internal_count_launches(1);
+    wait_selftest_kernel<<<1, 32, 0, st>>>(d);
+    TN_CUDA_TRY(cudaGetLastError());
+    TN_CUDA_TRY(cudaMemcpyAsync(&h, d, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    TN_CUDA_TRY(cudaFreeAsync(d, st));
+    TN_CUDA_TRY(cudaStreamSynchronize(st));
+    return (tn_status)h;
 }

@@ -48,6 +48,7 @@ constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 
 // event flags stored in the grp array once scheduling is done
+constexpr uint32_t kFlagDir = 1u << 27;   // directed event outside a tie group: one ONEWAY
 constexpr uint32_t kFlagNoop = 1u << 28;
 constexpr uint32_t kFlagIso = 1u << 29;
 constexpr uint32_t kFlagShA = 1u << 30;
@@ -75,6 +76,7 @@ struct PlanArgs {
     uint32_t n;
     const int64_t *t_after;
     uint32_t window;     // target events per window
+    uint32_t directed;   // 1: events are u -> v (only S[v] is updated)
     uint32_t nw;         // number of windows
     uint64_t *wstart;    // [nw + 1]
     uint32_t smem_max_events;
@@ -245,6 +247,83 @@ __device__ void schedule_window(const PlanArgs &a, uint32_t w, uint32_t *arena)
         uint32_t nruns = 0, naux = 0, ntemp = 0, maxlev = 0;
         uint32_t *auxw = a.aux_stage + 3 * s;
         uint32_t i = 0;
+        while (i < E && a.directed) {
+            // directed events x -> y: only y is written.  A lone event is one
+            // ONEWAY y |= x; a tie group becomes one PULL per receiver (level
+            // L+1) over its senders' rows, a sender that also receives in the
+            // group being read from a copy saved at level L.
+            const uint32_t g = grp[i];
+            uint32_t g1 = i + 1;
+            while (g1 < E && grp[g1] == g) ++g1;
+            if (g1 == i + 1) {
+                const uint32_t x = lu[i], y = lv[i];
+                if (x == y) {
+                    grp[i] = kFlagNoop;
+                } else {
+                    const uint32_t L = 1 + max(nlev[x], nlev[y]);
+                    nlev[x] = L;
+                    nlev[y] = L;
+                    evl[i] = L;
+                    grp[i] = kFlagDir;
+                    maxlev = max(maxlev, L);
+                }
+                i = g1;
+                continue;
+            }
+            for (uint32_t j = i; j < g1; ++j) {
+                ncnt[lv[j]] = 0;
+                nrun[lu[j]] = kNone;
+                nrun[lv[j]] = kNone;
+            }
+            uint32_t Lc = 0;
+            bool any = false;
+            for (uint32_t j = i; j < g1; ++j) {
+                if (lu[j] == lv[j]) continue;
+                ++ncnt[lv[j]];
+                Lc = max(Lc, max(nlev[lu[j]], nlev[lv[j]]));
+            }
+            const uint32_t run0 = nruns;
+            for (uint32_t j = i; j < g1; ++j) {  // one run per receiver
+                const uint32_t y = lv[j];
+                if (lu[j] == y || nrun[y] != kNone) continue;
+                const uint32_t ry = nruns++;
+                nrun[y] = ry;
+                run_node[ry] = y;
+                run_aux[ry] = naux;
+                run_lev[ry] = 0;  // fill counter until the level is known
+                run_temp[ry] = kNone;
+                auxw[naux] = ncnt[y];
+                naux += 1 + ncnt[y];
+            }
+            for (uint32_t j = i; j < g1; ++j) {
+                const uint32_t x = lu[j], y = lv[j];
+                if (x == y) {
+                    grp[j] = kFlagNoop;
+                    continue;
+                }
+                any = true;
+                grp[j] = kFlagShA | kFlagShB;  // no op of its own: the receiver's PULL covers it
+                uint32_t ref = x;
+                const uint32_t rx = nrun[x];
+                if (rx != kNone) {  // x also receives in this group: read its saved old row
+                    if (run_temp[rx] == kNone) run_temp[rx] = ntemp++;
+                    ref = kTempRef | run_temp[rx];
+                }
+                const uint32_t ry = nrun[y];
+                auxw[run_aux[ry] + 1 + run_lev[ry]++] = ref;
+            }
+            if (any) {
+                const uint32_t L = Lc + 1;
+                for (uint32_t j = i; j < g1; ++j) {
+                    if (grp[j] & kFlagNoop) continue;
+                    nlev[lu[j]] = L + 1;
+                    nlev[lv[j]] = L + 1;
+                }
+                for (uint32_t r = run0; r < nruns; ++r) run_lev[r] = L;
+                maxlev = max(maxlev, L + 1);
+            }
+            i = g1;
+        }
         while (i < E) {
             const uint32_t g = grp[i];
             uint32_t g1 = i + 1;
@@ -365,7 +444,7 @@ __device__ void schedule_window(const PlanArgs &a, uint32_t w, uint32_t *arena)
     for (uint32_t i = tid; i < E; i += T) {
         const uint32_t f = grp[i];
         if (f & kFlagNoop) continue;
-        if (f & kFlagIso) {
+        if (f & (kFlagIso | kFlagDir)) {
             atomicAdd(&lh[evl[i] - 1], 1u);
         } else {
             if (!(f & kFlagShA)) atomicAdd(&lh[evl[i] - 1], 1u);
@@ -412,6 +491,10 @@ __device__ void schedule_window(const PlanArgs &a, uint32_t w, uint32_t *arena)
             const uint32_t f = grp[i];
             if (f & kFlagNoop) continue;
             const uint32_t x = lu[i], y = lv[i];
+            if (f & kFlagDir) {
+                rops[atomicAdd(&lh[evl[i] - 1], 1u)] = local_op(kOneway, y, x);  // y |= x
+                continue;
+            }
             const uint32_t L = evl[i] - 1;
             if (f & kFlagIso) {
                 rops[atomicAdd(&lh[L], 1u)] = local_op(kEvent, x, y);
@@ -460,6 +543,10 @@ __device__ void schedule_window(const PlanArgs &a, uint32_t w, uint32_t *arena)
         if (f & kFlagNoop) continue;
         const uint32_t x = U[i], y = V[i];
         const uint32_t L = evl[i] - 1;
+        if (f & kFlagDir) {
+            ops[atomicAdd(&lh[L], 1u)] = make_uint2(op_a(kOneway, y), x);  // y |= x
+            continue;
+        }
         if (f & kFlagIso) {
             ops[atomicAdd(&lh[L], 1u)] = make_uint2(op_a(kEvent, x), y);
         } else {
@@ -634,8 +721,9 @@ extern "C" tn_status tn_plan_create(const uint32_t *u, const uint32_t *v, const 
     if (!u || !v || !t || m == 0 || n == 0 || n >= (1u << 30) || m >= (1ull << 30)) return TN_EINVAL;
     uint32_t sw = kDefaultSlab, window = kDefaultWindow, rows = 0;
     if (opt) {
-        for (int i = 0; i < 5; ++i)
+        for (int i = 0; i < 4; ++i)
             if (opt->reserved[i]) return TN_EINVAL;
+        if (opt->directed > 1) return TN_EINVAL;
         if (opt->slab_words) sw = opt->slab_words;
         if (opt->window_events) window = opt->window_events;
         rows = opt->smem_rows;
@@ -657,6 +745,7 @@ extern "C" tn_status tn_plan_create(const uint32_t *u, const uint32_t *v, const 
     a.n = n;
     a.t_after = t_after;
     a.window = window;
+    a.directed = opt ? opt->directed : 0u;
     a.nw = (uint32_t)((m + window - 1) / window);
     a.smem_max_events = smem_max_events();
     a.dcap = rows;

@@ -467,3 +467,65 @@ def test_reversed_rejects_streaming_use():
     assert exc.value.status == tn.TN_EINVAL
     with pytest.raises(tn.TnError):
         tn.tn_component_matrix(du, dv, dt, n, init=False, reverse=True)
+
+
+# --------------------------------------------------------------------------
+# failure handling: bounded device waits
+# --------------------------------------------------------------------------
+def test_bounded_wait_times_out_and_context_survives():
+    """A wait on a barrier that nothing completes gives up with TN_ETIMEOUT
+    (no trap, no hang), and the next call works."""
+    assert tn.tn_selftest_wait_timeout() == tn.TN_ETIMEOUT
+    u, v, t = synth.uniform_events(100, 500, t_range=200, seed=6)
+    assert np.array_equal(gpu_matrix(u, v, t, 100), oracle.component_matrix(u, v, t, 100))
+
+
+# --------------------------------------------------------------------------
+# directed events (footnote to Section 3.1)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("n,m,t_range,slab,smem_rows,seed", [
+    (400, 8000, 8000, 16, 0, 1),    # mostly lone events: ONEWAY ops in shared memory
+    (400, 8000, 300, 8, 0, 2),      # small tie groups: PULL runs with saved rows
+    (900, 20_000, 12, 16, 0, 3),    # giant groups: global tiles
+    (900, 20_000, 40, 4, 1, 4),     # every window through the global path
+    (70, 5000, 9000, 2, 0, 5),
+])
+def test_directed_matches_oracle(n, m, t_range, slab, smem_rows, seed):
+    u, v, t = synth.uniform_events(n, m, t_range=t_range, seed=seed, self_loops=True)
+    du, dv, dt = dev_events(u, v, t)
+    plan = tn.Plan(du, dv, dt, n, slab_words=slab, smem_rows=smem_rows, directed=True)
+    S = plan.apply(None, init=True)
+    assert plan.status() == 0
+    want = oracle.component_matrix_directed(u, v, t, n)
+    assert np.array_equal(host_matrix(S, n), want)
+    out, _, _ = tn.tn_out_sizes(S, n, n)
+    assert np.array_equal(u32(out), oracle.column_counts(want, n))
+
+
+def test_directed_doubled_equals_undirected_and_reverse_transposes():
+    n, m = 600, 15_000
+    u, v, t = synth.uniform_events(n, m, t_range=900, seed=9, self_loops=True)
+    du2 = np.stack([u, v], 1).reshape(-1)
+    dv2 = np.stack([v, u], 1).reshape(-1)
+    dt2 = np.repeat(t, 2)
+    a, b, c = dev_events(du2, dv2, dt2)
+    D = host_matrix(tn.tn_component_matrix(a, b, c, n, directed=True), n)
+    assert np.array_equal(D, oracle.component_matrix(u, v, t, n))
+    du, dv, dt = dev_events(u, v, t)
+    F = oracle.to_bool(host_matrix(tn.tn_component_matrix(du, dv, dt, n, directed=True), n), n)
+    R = oracle.to_bool(host_matrix(tn.tn_component_matrix(du, dv, dt, n, directed=True, reverse=True), n), n)
+    torch.cuda.synchronize()
+    assert np.array_equal(R, F.T)
+
+
+def test_directed_incremental_batches():
+    n, m = 500, 12_000
+    u, v, t = synth.uniform_events(n, m, t_range=3000, seed=10)
+    parts = synth.split_batches(t, 4)
+    S = torch.empty((n, tn.tn_row_words(n)), dtype=torch.int64, device="cuda")
+    t_last = torch.full((1,), -(2**62), dtype=torch.int64, device="cuda")
+    for k, (a, b) in enumerate(parts):
+        du, dv, dt = dev_events(u[a:b], v[a:b], t[a:b])
+        tn.tn_component_matrix(du, dv, dt, n, S=S, t_last=t_last, init=(k == 0), directed=True)
+    torch.cuda.synchronize()
+    assert np.array_equal(host_matrix(S, n), oracle.component_matrix_directed(u, v, t, n))
