@@ -12,6 +12,8 @@ arrays.  Functions cite the paper passage they follow:
 * ``component_matrix_reversed`` -- the reversed-sequence variant (Section 3.4).
 * ``component_matrix_directed`` / ``si_reach_directed`` -- directed events
   (footnote to Section 3.1: only the receiver's row is updated).
+* ``hll_singleton`` / ``hll_sketches`` / ``hll_estimate`` -- HyperLogLog
+  sketches of the components and their size estimates (Section 3.4).
 * ``si_reach``          -- the deterministic SI process (Section 1).
 * ``column_counts`` / ``row_counts`` / ``argmax`` -- component sizes
   (Section 3.1, eq. for the mean size s_t in Section 3.3).
@@ -48,7 +50,7 @@ def build_oracle(force: bool = False) -> str:
     """Compile tnref.c into libtnref.so next to it (plain gcc, no CUDA)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -74,6 +76,15 @@ def _load():
         lib.tnref_apply_events_directed.restype = ctypes.c_int
         lib.tnref_si_reach_directed.argtypes = [_u32p, _u32p, _i64p, ctypes.c_uint64, ctypes.c_uint32,
                                                 ctypes.c_uint32, _u8p]
+        lib.tnref_hll_singleton.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                            ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint8)]
+        lib.tnref_hll_singleton.restype = None
+        lib.tnref_hll_sketches.argtypes = [_u32p, _u32p, _i64p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                           ctypes.c_uint64, ctypes.c_int, ctypes.c_int, _u8p]
+        lib.tnref_hll_sketches.restype = ctypes.c_int
+        lib.tnref_hll_estimate.argtypes = [_u8p, ctypes.c_uint32, ctypes.c_uint32,
+                                           np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")]
+        lib.tnref_hll_estimate.restype = None
         lib.tnref_si_reach_directed.restype = ctypes.c_int
         lib.tnref_si_reach.argtypes = [_u32p, _u32p, _i64p, ctypes.c_uint64, ctypes.c_uint32,
                                        ctypes.c_uint32, _u8p]
@@ -301,3 +312,27 @@ def error_stats(est, exact) -> dict:
     return dict(count=c, sum_abs=sa.value, max_abs=ma.value, w1_num=wn.value, rel_sum=rs.value,
                 max_rel=mr.value, mean_abs=sa.value / c if c else 0.0, mean_rel=rs.value / c if c else 0.0,
                 w1=wn.value / c if c else 0.0)
+
+
+def hll_singleton(seed: int, p: int, x: int):
+    """(register, rank) of element x in a sketch of 2^p registers (Section 3.4)."""
+    reg, rank = ctypes.c_uint32(), ctypes.c_uint8()
+    _load().tnref_hll_singleton(seed, p, x, ctypes.byref(reg), ctypes.byref(rank))
+    return reg.value, rank.value
+
+
+def hll_sketches(u, v, t, n: int, p: int, seed: int, reverse: bool = False, directed: bool = False) -> np.ndarray:
+    """uint8[n, 2^p]: node i's sketch of its in-component (out-component with
+    reverse=True), merged by register-wise maximum per event (Section 3.4)."""
+    u, v, t = _ev(u, v, t)
+    R = np.zeros((n, 1 << p), dtype=np.uint8)
+    _check(_load().tnref_hll_sketches(u, v, t, len(u), n, p, seed, int(reverse), int(directed), R.reshape(-1)))
+    return R
+
+
+def hll_estimate(R: np.ndarray, p: int) -> np.ndarray:
+    """float64[n] HyperLogLog size estimates of the sketches."""
+    R = np.ascontiguousarray(R, dtype=np.uint8)
+    est = np.zeros(R.shape[0], dtype=np.float64)
+    _load().tnref_hll_estimate(R.reshape(-1), R.shape[0], p, est)
+    return est

@@ -32,6 +32,7 @@
  * structure and 4-wise independence are pinned, but agreement with the
  * authors' own (unpublished) hash values is "parity unpinned".
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -553,4 +554,152 @@ int tnref_si_reach_directed(const uint32_t *u, const uint32_t *v, const int64_t 
     }
     free(fresh);
     return TNREF_OK;
+}
+
+/* ---------------------------------------------------------------------------
+ * HyperLogLog sketches of the components (Section 3.4; Flajolet, Fusy,
+ * Gandouet, Meunier 2007).  Each node keeps s = 2^p one-byte registers.  An
+ * element x hashes to h = one SplitMix64 step from state (seed XOR x); its
+ * register is the top p bits of h and its rank the position of the first 1 in
+ * the remaining 64 - p bits (64 - p + 1 if they are all 0).  Node i starts as
+ * the sketch of {i}; an event merges sketches by register-wise maximum with
+ * the same snapshot rule per timestamp group as the component matrix, so that
+ * node i's sketch is always the sketch of its in-component (of its
+ * out-component when the sequence is processed in reverse).  The estimate of
+ * a sketch M is E = alpha_s s^2 / sum_j 2^(-M[j]), replaced by linear counting
+ * s ln(s / V) when E <= 2.5 s and V > 0 registers are zero.
+ * ------------------------------------------------------------------------- */
+void tnref_hll_singleton(uint64_t seed, uint32_t p, uint32_t x, uint32_t *reg, uint8_t *rank)
+{
+    uint64_t st = seed ^ (uint64_t)x;
+    uint64_t h = splitmix64_next(&st);
+    *reg = (uint32_t)(h >> (64 - p));
+    uint64_t w = h << p;
+    uint32_t r = 1;
+    while (r <= 64 - p && !(w & (1ull << 63))) {
+        ++r;
+        w <<= 1;
+    }
+    *rank = (uint8_t)r;
+}
+
+static void hll_merge_group(const uint32_t *u, const uint32_t *v, uint64_t g0, uint64_t g1, uint8_t *R,
+                            uint32_t s, int directed, int turn, uint8_t *old, int64_t *slot,
+                            uint32_t *touched)
+{
+    uint64_t nt = 0;
+    for (uint64_t e = g0; e < g1; ++e) {
+        uint32_t a = turn ? v[e] : u[e], b = turn ? u[e] : v[e];
+        uint32_t ends[2] = {a, b};
+        for (int q = 0; q < (directed ? 1 : 2); ++q) { /* rows that are read: senders (directed) or both ends */
+            uint32_t x = ends[q];
+            if (slot[x] < 0) {
+                slot[x] = (int64_t)nt;
+                touched[nt] = x;
+                memcpy(old + nt * s, R + (uint64_t)x * s, s);
+                ++nt;
+            }
+        }
+    }
+    for (uint64_t e = g0; e < g1; ++e) {
+        uint32_t a = turn ? v[e] : u[e], b = turn ? u[e] : v[e];
+        uint8_t *rb = R + (uint64_t)b * s;
+        const uint8_t *oa = old + (uint64_t)slot[a] * s;
+        for (uint32_t j = 0; j < s; ++j)
+            if (oa[j] > rb[j])
+                rb[j] = oa[j];
+        if (!directed) {
+            uint8_t *ra = R + (uint64_t)a * s;
+            const uint8_t *ob = old + (uint64_t)slot[b] * s;
+            for (uint32_t j = 0; j < s; ++j)
+                if (ob[j] > ra[j])
+                    ra[j] = ob[j];
+        }
+    }
+    for (uint64_t k = 0; k < nt; ++k)
+        slot[touched[k]] = -1;
+}
+
+/* R: n x 2^p registers.  reverse: groups from the last to the first (and
+ * directed events turned around), so row i sketches the out-component of i. */
+int tnref_hll_sketches(const uint32_t *u, const uint32_t *v, const int64_t *t, uint64_t m, uint32_t n,
+                       uint32_t p, uint64_t seed, int reverse, int directed, uint8_t *R)
+{
+    if (p < 4 || p > 16)
+        return TNREF_EINVAL;
+    int rc = tnref_validate(u, v, t, m, n);
+    if (rc != TNREF_OK)
+        return rc;
+    const uint32_t s = 1u << p;
+    memset(R, 0, (size_t)n * s);
+    for (uint32_t i = 0; i < n; ++i) {
+        uint32_t reg;
+        uint8_t rank;
+        tnref_hll_singleton(seed, p, i, &reg, &rank);
+        R[(uint64_t)i * s + reg] = rank;
+    }
+    if (m == 0)
+        return TNREF_OK;
+    int64_t *slot = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    uint32_t *touched = (uint32_t *)malloc(2 * m * sizeof(uint32_t));
+    uint8_t *old = (uint8_t *)malloc(2 * m * (size_t)s);
+    if (!slot || !touched || !old) {
+        free(slot);
+        free(touched);
+        free(old);
+        return TNREF_ENOMEM;
+    }
+    for (uint32_t i = 0; i < n; ++i)
+        slot[i] = -1;
+    const int turn = reverse && directed;
+    if (!reverse) {
+        uint64_t g0 = 0;
+        while (g0 < m) {
+            uint64_t g1 = g0 + 1;
+            while (g1 < m && t[g1] == t[g0])
+                ++g1;
+            hll_merge_group(u, v, g0, g1, R, s, directed, turn, old, slot, touched);
+            g0 = g1;
+        }
+    } else {
+        uint64_t g1 = m;
+        while (g1 > 0) {
+            uint64_t g0 = g1 - 1;
+            while (g0 > 0 && t[g0 - 1] == t[g1 - 1])
+                --g0;
+            hll_merge_group(u, v, g0, g1, R, s, directed, turn, old, slot, touched);
+            g1 = g0;
+        }
+    }
+    free(slot);
+    free(touched);
+    free(old);
+    return TNREF_OK;
+}
+
+void tnref_hll_estimate(const uint8_t *R, uint32_t n, uint32_t p, double *est)
+{
+    const uint32_t s = 1u << p;
+    double alpha;
+    if (s == 16)
+        alpha = 0.673;
+    else if (s == 32)
+        alpha = 0.697;
+    else if (s == 64)
+        alpha = 0.709;
+    else
+        alpha = 0.7213 / (1.0 + 1.079 / (double)s);
+    for (uint32_t i = 0; i < n; ++i) {
+        const uint8_t *M = R + (uint64_t)i * s;
+        double z = 0.0;
+        uint32_t zeros = 0;
+        for (uint32_t j = 0; j < s; ++j) {
+            z += ldexp(1.0, -(int)M[j]);
+            zeros += M[j] == 0;
+        }
+        double e = alpha * (double)s * (double)s / z;
+        if (e <= 2.5 * (double)s && zeros > 0)
+            e = (double)s * log((double)s / (double)zeros);
+        est[i] = e;
+    }
 }

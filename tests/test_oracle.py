@@ -504,3 +504,75 @@ def test_directed_exhaustive_tiny():
                 B = oracle.to_bool(oracle.component_matrix_directed(u, v, t, 3), 3)
                 for j in range(3):
                     assert np.array_equal(B[:, j], oracle.si_reach_directed(u, v, t, 3, j))
+
+
+# --------------------------------------------------------------------------
+# HyperLogLog sketches of the components (Section 3.4)
+# --------------------------------------------------------------------------
+def _singletons(seed, p, n):
+    s = 1 << p
+    S1 = np.zeros((n, s), np.uint8)
+    for x in range(n):
+        reg, rank = oracle.hll_singleton(seed, p, x)
+        S1[x, reg] = rank
+    return S1
+
+
+@pytest.mark.parametrize("reverse,directed", [(False, False), (True, False), (False, True), (True, True)])
+def test_hll_sketch_is_the_union_of_its_members(reverse, directed):
+    """A node's sketch equals the register-wise maximum of the singleton
+    sketches of exactly the members of its component (the exact matrix), in
+    every mode: the merge rule commutes with set union."""
+    n, m, p, seed = 60, 700, 6, 11
+    u, v, t = synth.uniform_events(n, m, t_range=120, seed=3, self_loops=True)
+    R = oracle.hll_sketches(u, v, t, n, p, seed, reverse=reverse, directed=directed)
+    if directed:
+        F = oracle.to_bool(oracle.component_matrix_directed(u, v, t, n), n)
+    else:
+        F = oracle.to_bool(oracle.component_matrix(u, v, t, n), n)
+    members = F.T if reverse else F  # row i: members of i's component
+    S1 = _singletons(seed, p, n)
+    for i in range(n):
+        assert np.array_equal(R[i], S1[members[i]].max(axis=0)), i
+
+
+def test_hll_rank_distribution():
+    """P(rank = r) = 2^-r and registers are uniform (the hash's job)."""
+    p, N = 8, 40_000
+    regs = np.zeros(N, np.int64)
+    ranks = np.zeros(N, np.int64)
+    for x in range(N):
+        regs[x], ranks[x] = oracle.hll_singleton(17, p, x)
+    for r in range(1, 6):
+        assert abs((ranks == r).mean() - 2.0 ** -r) < 4 * np.sqrt(2.0 ** -r / N)
+    counts = np.bincount(regs, minlength=1 << p)
+    assert counts.min() > 0.6 * N / (1 << p) and counts.max() < 1.4 * N / (1 << p)
+
+
+@pytest.mark.parametrize("p", [7, 10])
+def test_hll_estimate_accuracy(p):
+    """Estimates of sets of many sizes stay within the HLL error: the mean
+    relative error is a few times 1.04 / sqrt(2^p), small sets are exact-ish
+    (linear counting)."""
+    s = 1 << p
+    rng = np.random.default_rng(p)
+    S1 = _singletons(23, p, 30_000)
+    rel = []
+    for N in (5, 50, 500, 5000, 30_000):
+        for _ in range(4):
+            idx = rng.choice(30_000, N, replace=False)
+            e = oracle.hll_estimate(S1[idx].max(axis=0)[None, :], p)[0]
+            rel.append(abs(e / N - 1.0))
+            if N <= s // 10:
+                assert abs(e - N) <= max(1.0, 0.05 * N)
+    assert np.mean(rel) < 3 * 1.04 / np.sqrt(s)
+
+
+def test_hll_estimate_formula_hand_values():
+    p = 4  # s = 16, alpha = 0.673
+    empty = np.zeros((1, 16), np.uint8)
+    assert oracle.hll_estimate(empty, p)[0] == 0.0  # linear counting: 16 ln(16/16)
+    one = empty.copy(); one[0, 3] = 1
+    assert oracle.hll_estimate(one, p)[0] == pytest.approx(16 * np.log(16 / 15), rel=1e-15)
+    full = np.full((1, 16), 5, np.uint8)  # no zero register: the raw estimate
+    assert oracle.hll_estimate(full, p)[0] == pytest.approx(0.673 * 256 / (16 * 2.0 ** -5), rel=1e-15)
