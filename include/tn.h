@@ -450,6 +450,35 @@ tn_status tn_server_get_stats(tn_server *server, tn_server_stats *stats);
 tn_status tn_server_destroy(tn_server *server);
 
 /* ---------------------------------------------------------------------------
+ * HyperLogLog sketches of the components (Section 3.4).  Approximate: O(n s)
+ * memory instead of n^2 bits, for the average component size (in-components,
+ * Eq. s_t) or, with TN_REVERSE, the out-component size distribution.
+ *
+ * Node i keeps s = 2^p one-byte registers (4 <= p <= 16).  Element x hashes to
+ * h = one SplitMix64 step (Steele, Lea, Flood 2014) from state (seed XOR x);
+ * its register is the top p bits of h, its rank the position of the first 1
+ * among the remaining 64 - p bits (64 - p + 1 if none).  Node i starts as the
+ * sketch of {i}; every event merges sketches by register-wise maximum under
+ * the same rules as the component matrix (snapshot timestamp groups, flags
+ * TN_REVERSE and TN_DIRECTED as for tn_component_matrix), so row i is exactly
+ * the sketch of node i's in-component (out-component when reversed).
+ *
+ *   R    uint8, n rows of tn_hll_row_bytes(p) bytes (a multiple of 128),
+ *        16-byte aligned; register j of node i is R[i * row_bytes + j].
+ * Validating and synchronous (TN_ERANGE for an endpoint >= n).
+ */
+uint64_t tn_hll_row_bytes(uint32_t p);  /* 0 for p outside [4, 16] */
+tn_status tn_hll_sketches(const uint32_t *u, const uint32_t *v, const int64_t *t, uint64_t m,
+                          uint32_t n, uint32_t p, uint64_t seed, uint32_t flags, uint8_t *R,
+                          void *stream);
+
+/* est[i] = alpha_s s^2 / sum_j 2^(-M[j]) for node i's registers M (alpha_16
+ * 0.673, alpha_32 0.697, alpha_64 0.709, else 0.7213 / (1 + 1.079 / s)),
+ * replaced by linear counting s ln(s / V) when it is <= 2.5 s and V > 0
+ * registers are zero (Flajolet et al. 2007).  est: double[n].  Asynchronous. */
+tn_status tn_hll_estimate(const uint8_t *R, uint32_t n, uint32_t p, double *est, void *stream);
+
+/* ---------------------------------------------------------------------------
  * tn_selftest_wait_timeout -- exercises the bounded device waits that every
  * kernel of this library uses instead of unbounded spins: a kernel waits on a
  * barrier that nothing completes and gives up after its poll limit (a few

@@ -24,6 +24,7 @@ __all__ = [
     "tn_hash_proxy", "tn_hash_estimate", "tn_hash_estimate_noalloc", "tn_error_stats",
     "tn_out_component_sizes_host",
     "Plan", "tn_plan_apply_batch", "Server", "BatchGraph", "tn_autotune", "tn_selftest_wait_timeout",
+    "tn_hll_sketches", "tn_hll_estimate",
     "TN_OK", "TN_EINVAL", "TN_ERANGE", "TN_EORDER", "TN_ENOMEM", "TN_ECUDA", "TN_ETIMEOUT", "TN_ESCRATCH",
     "TN_INIT_IDENTITY", "TN_REVERSE", "TN_DIRECTED",
 ]
@@ -127,6 +128,9 @@ def load_library(path: str | None = None):
         "tn_graph_destroy": ([vp], i32),
         "tn_autotune": ([vp, vp, vp, u64, u32, u32, u32, u64, vp, ctypes.POINTER(_TuneResult)], i32),
         "tn_selftest_wait_timeout": ([vp], i32),
+        "tn_hll_row_bytes": ([u32], u64),
+        "tn_hll_sketches": ([vp, vp, vp, u64, u32, u32, u64, u32, vp, vp], i32),
+        "tn_hll_estimate": ([vp, u32, u32, vp, vp], i32),
         "tn_server_create": ([ctypes.POINTER(_ServerOptions), ctypes.POINTER(vp)], i32),
         "tn_server_submit": ([vp, u64, u32, vp, vp, vp, vp, u32, vp, vp], i32),
         "tn_server_poll": ([vp, ctypes.POINTER(_JobRecord), u32, ctypes.POINTER(u32), u32], i32),
@@ -527,3 +531,28 @@ class BatchGraph:
 def tn_selftest_wait_timeout(stream=None) -> int:
     """Runs the bounded-wait self-test; returns its status (TN_ETIMEOUT expected)."""
     return int(load_library().tn_selftest_wait_timeout(_stream(stream)))
+
+
+def tn_hll_sketches(u, v, t, n: int, p: int, seed: int, reverse: bool = False, directed: bool = False, stream=None):
+    """HyperLogLog sketches of the components (Section 3.4): uint8 [n, row_bytes];
+    the first 2^p bytes of row i are node i's registers."""
+    torch = _torch()
+    lib = load_library()
+    m = _events(u, v, t)
+    rb = int(lib.tn_hll_row_bytes(p))
+    if rb == 0:
+        raise ValueError("p must be in [4, 16]")
+    R = torch.empty((n, rb), dtype=torch.uint8, device=u.device)
+    flags = (TN_REVERSE if reverse else 0) | (TN_DIRECTED if directed else 0)
+    _check(lib.tn_hll_sketches(_ptr(u), _ptr(v), _ptr(t), m, n, p, seed & (2**64 - 1), flags, _ptr(R),
+                               _stream(stream)), "tn_hll_sketches")
+    return R
+
+
+def tn_hll_estimate(R, n: int, p: int, stream=None):
+    """float64[n] size estimates of the sketches."""
+    torch = _torch()
+    lib = load_library()
+    est = torch.empty(n, dtype=torch.float64, device=R.device)
+    _check(lib.tn_hll_estimate(_ptr(R), n, p, _ptr(est), _stream(stream)), "tn_hll_estimate")
+    return est

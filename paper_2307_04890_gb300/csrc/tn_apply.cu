@@ -132,6 +132,7 @@ __device__ inline void sts16(u64x2 *p, u64x2 v)
 // global tile: ops name rows by node id and read/write the matrix directly
 // ---------------------------------------------------------------------------
 // PULL: S[x] |= OR of the listed source rows (aux[b] = count, then refs)
+template <bool kMax>
 __device__ inline void apply_pull(const Job &J, uint32_t x, uint32_t b, uint64_t col)
 {
     uint64_t *pd = J.S + (uint64_t)x * J.ld + col;
@@ -146,12 +147,13 @@ __device__ inline void apply_pull(const Job &J, uint32_t x, uint32_t b, uint64_t
         for (int k = 0; k < 8; ++k)
             r[k] = (ref[k] != kNoRef) ? ld_row16(row_ptr(J, ref[k], col)) : u64x2{0, 0};
 #pragma unroll
-        for (int k = 0; k < 8; ++k) acc = or16(acc, r[k]);
+        for (int k = 0; k < 8; ++k) acc = combine16<kMax>(acc, r[k]);
     }
     st_row16(pd, acc);
 }
 
 // Direct form, for row buffers too small to stage a chunk: four ops in flight per thread.
+template <bool kMax>
 __device__ inline void apply_tile_direct(const Job &J, const uint2 *ops, uint32_t count, const Lane &L)
 {
     if (!L.active) return;  // partial last slab, or a thread outside the row groups
@@ -183,7 +185,7 @@ __device__ inline void apply_tile_direct(const Job &J, const uint2 *ops, uint32_
             if (kind == kCopy) {
                 st_row16(J.tmp + ia, rb[k]);
             } else {
-                const u64x2 r = or16(ra[k], rb[k]);
+                const u64x2 r = combine16<kMax>(ra[k], rb[k]);
                 st_row16(J.S + ia, r);
                 if (kind == kEvent) st_row16(J.S + (uint64_t)op[k].y * J.ld + col, r);
             }
@@ -192,7 +194,7 @@ __device__ inline void apply_tile_direct(const Job &J, const uint2 *ops, uint32_
     // multi-source updates of tie groups (hub rows) in a second pass
     for (uint32_t o = L.lane0; o < count; o += stride) {
         const uint2 op = ops[o];
-        if ((op.x >> kKindShift) == kPull) apply_pull(J, op.x & kIdMask, op.y, col);
+        if ((op.x >> kKindShift) == kPull) apply_pull<kMax>(J, op.x & kIdMask, op.y, col);
     }
 }
 
@@ -200,13 +202,14 @@ __device__ inline void apply_tile_direct(const Job &J, const uint2 *ops, uint32_
 // first copied into shared memory (private slots 2i and 2i+1 for op i, so no
 // lookup is needed and every copy is in flight at once), then each op's
 // result goes from registers straight to its destination rows.
+template <bool kMax>
 __device__ inline void apply_tile(const Job &J, const uint2 *ops, uint32_t count, u64x2 *buf, uint32_t dcap,
                                   const Lane &L)
 {
     const uint32_t cpr = L.cpr, stride = L.stride;
     const uint64_t col = L.col;
     if (dcap < 64) {
-        apply_tile_direct(J, ops, count, L);
+        apply_tile_direct<kMax>(J, ops, count, L);
         return;
     }
     const uint32_t chunk_ops = dcap / 2;
@@ -234,7 +237,7 @@ __device__ inline void apply_tile(const Job &J, const uint2 *ops, uint32_t count
                 if (kind == kCopy) {
                     st_row16(J.tmp + ia, rb);
                 } else {
-                    const u64x2 r = or16(lds16(mine + (2 * i) * cpr), rb);
+                    const u64x2 r = combine16<kMax>(lds16(mine + (2 * i) * cpr), rb);
                     st_row16(J.S + ia, r);
                     if (kind == kEvent) st_row16(J.S + (uint64_t)op.y * J.ld + col, r);
                 }
@@ -246,7 +249,7 @@ __device__ inline void apply_tile(const Job &J, const uint2 *ops, uint32_t count
     // multi-source updates of tie groups (hub rows) in a second pass
     for (uint32_t o = L.lane0; o < count; o += stride) {
         const uint2 op = ops[o];
-        if ((op.x >> kKindShift) == kPull) apply_pull(J, op.x & kIdMask, op.y, col);
+        if ((op.x >> kKindShift) == kPull) apply_pull<kMax>(J, op.x & kIdMask, op.y, col);
     }
 }
 
@@ -254,6 +257,7 @@ __device__ inline void apply_tile(const Job &J, const uint2 *ops, uint32_t count
 // local record: the window's rows are gathered into shared memory, its levels
 // are applied there, and the rows are written back
 // ---------------------------------------------------------------------------
+template <bool kMax>
 __device__ inline void apply_record(const Job &J, const uint32_t *rec, u64x2 *buf, const Lane &L)
 {
     const uint32_t D = rec[0], nlev = rec[2], nops = rec[3];
@@ -300,17 +304,17 @@ __device__ inline void apply_record(const Job &J, const uint32_t *rec, u64x2 *bu
                 for (int k = 0; k < 2; ++k) {
                     const uint32_t kind = op[k] >> kKindShift, a = (op[k] >> 15) & kLocalMask, b = op[k] & kLocalMask;
                     if (kind == kEvent) {
-                        const u64x2 r = or16(x[k], y[k]);
+                        const u64x2 r = combine16<kMax>(x[k], y[k]);
                         sts16(mine + a * cpr, r);
                         sts16(mine + b * cpr, r);
                     } else if (kind == kOneway) {
-                        sts16(mine + a * cpr, or16(x[k], y[k]));
+                        sts16(mine + a * cpr, combine16<kMax>(x[k], y[k]));
                     } else if (kind == kCopy) {
                         sts16(mine + a * cpr, y[k]);
                     } else if (live[k]) {
                         u64x2 acc = lds16(mine + a * cpr);
                         const uint32_t c = aux[b];
-                        for (uint32_t q = 1; q <= c; ++q) acc = or16(acc, lds16(mine + aux[b + q] * cpr));
+                        for (uint32_t q = 1; q <= c; ++q) acc = combine16<kMax>(acc, lds16(mine + aux[b + q] * cpr));
                         sts16(mine + a * cpr, acc);
                     }
                 }
@@ -335,6 +339,7 @@ __device__ inline void apply_record(const Job &J, const uint32_t *rec, u64x2 *bu
     }
 }
 
+template <bool kMax>
 __global__ void __launch_bounds__(kThreads) stream_kernel(const __grid_constant__ JobList jl)
 {
     extern __shared__ __align__(128) uint8_t smem[];
@@ -430,9 +435,9 @@ __global__ void __launch_bounds__(kThreads) stream_kernel(const __grid_constant_
             // item's loads, and all consumers agree on stopping
             if (consumers_sync_or(stop)) break;
             if (hdr[s].local) {
-                apply_record(J, reinterpret_cast<const uint32_t *>(stage + (size_t)s * kStageBytes), rowbuf, L);
+                apply_record<kMax>(J, reinterpret_cast<const uint32_t *>(stage + (size_t)s * kStageBytes), rowbuf, L);
             } else {
-                apply_tile(J, reinterpret_cast<const uint2 *>(stage + (size_t)s * kStageBytes) + hdr[s].off,
+                apply_tile<kMax>(J, reinterpret_cast<const uint2 *>(stage + (size_t)s * kStageBytes) + hdr[s].off,
                            hdr[s].count, rowbuf, J.dcap, L);
             }
             __syncwarp();
@@ -594,9 +599,14 @@ tn_status apply_jobs(const tn_plan *const *plans, uint64_t *const *S, const uint
         }
         TN_CUDA_TRY(cudaGetLastError());
         if (ctas) {
-            TN_CUDA_TRY(tn_internal_allow_max_dyn_smem((const void *)stream_kernel));
             tn_internal_count_launches(1);
-            stream_kernel<<<ctas, kThreads, smem, st>>>(jl);
+            if (flags & kApplyMax) {
+                TN_CUDA_TRY(tn_internal_allow_max_dyn_smem((const void *)stream_kernel<true>));
+                stream_kernel<true><<<ctas, kThreads, smem, st>>>(jl);
+            } else {
+                TN_CUDA_TRY(tn_internal_allow_max_dyn_smem((const void *)stream_kernel<false>));
+                stream_kernel<false><<<ctas, kThreads, smem, st>>>(jl);
+            }
         }
         TN_CUDA_TRY(cudaGetLastError());
         for (uint32_t j = 0; j < nj; ++j) {
@@ -653,6 +663,21 @@ static tn_status one_shot(const uint32_t *u, const uint32_t *v, const int64_t *t
                           const uint32_t *src, uint32_t ncols, uint64_t *S, int64_t *t_last, uint32_t flags,
                           void *stream);
 
+tn_status tn::reversed_events(const uint32_t *u, const uint32_t *v, const int64_t *t, uint64_t m, bool turn,
+                              uint32_t **ru, uint32_t **rv, int64_t **rt, cudaStream_t st)
+{
+    *ru = nullptr;
+    *rv = nullptr;
+    *rt = nullptr;
+    TN_CUDA_TRY(cudaMallocAsync((void **)ru, m * 4, st));
+    TN_CUDA_TRY(cudaMallocAsync((void **)rv, m * 4, st));
+    TN_CUDA_TRY(cudaMallocAsync((void **)rt, m * 8, st));
+    tn_internal_count_launches(1);
+    reverse_events_kernel<<<grid_for(m), 256, 0, st>>>(u, v, t, m, turn, *ru, *rv, *rt);
+    TN_CUDA_TRY(cudaGetLastError());
+    return TN_OK;
+}
+
 // TN_REVERSE: the same path over the reversed sequence, from the identity
 static tn_status one_shot_reversed(const uint32_t *u, const uint32_t *v, const int64_t *t, uint64_t m, uint32_t n,
                                    const uint32_t *src, uint32_t ncols, uint64_t *S, int64_t *t_last,
@@ -664,12 +689,8 @@ static tn_status one_shot_reversed(const uint32_t *u, const uint32_t *v, const i
     cudaStream_t st = (cudaStream_t)stream;
     uint32_t *ru = nullptr, *rv = nullptr;
     int64_t *rt = nullptr;
-    TN_CUDA_TRY(cudaMallocAsync((void **)&ru, m * 4, st));
-    TN_CUDA_TRY(cudaMallocAsync((void **)&rv, m * 4, st));
-    TN_CUDA_TRY(cudaMallocAsync((void **)&rt, m * 8, st));
-    tn_internal_count_launches(1);
-    reverse_events_kernel<<<grid_for(m), 256, 0, st>>>(u, v, t, m, (flags & TN_DIRECTED) != 0, ru, rv, rt);
-    TN_CUDA_TRY(cudaGetLastError());
+    const tn_status rr = reversed_events(u, v, t, m, (flags & TN_DIRECTED) != 0, &ru, &rv, &rt, st);
+    if (rr != TN_OK) return rr;
     const tn_status rc = one_shot(ru, rv, rt, m, n, src, ncols, S, nullptr, flags & ~TN_REVERSE, stream);
     cudaFreeAsync(ru, st);
     cudaFreeAsync(rv, st);

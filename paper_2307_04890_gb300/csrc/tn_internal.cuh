@@ -158,6 +158,22 @@ __device__ inline void st_row16(uint64_t *p, u64x2 r)
 
 __device__ inline u64x2 or16(u64x2 a, u64x2 b) { return u64x2{a.x | b.x, a.y | b.y}; }
 
+// Combine of two row chunks: OR of bitsets (component matrix), or byte-wise
+// maximum (HyperLogLog registers, one byte each).
+__device__ inline uint64_t max8x8(uint64_t a, uint64_t b)
+{
+    const uint32_t lo = __vmaxu4((uint32_t)a, (uint32_t)b);
+    const uint32_t hi = __vmaxu4((uint32_t)(a >> 32), (uint32_t)(b >> 32));
+    return ((uint64_t)hi << 32) | lo;
+}
+
+template <bool kMax>
+__device__ inline u64x2 combine16(u64x2 a, u64x2 b)
+{
+    if (kMax) return u64x2{max8x8(a.x, b.x), max8x8(a.y, b.y)};
+    return or16(a, b);
+}
+
 // ---------------------------------------------------------------------------
 // Block-wide exclusive scan of an array (generic pointer: shared or global).
 // All threads of the block must call it; returns the total.  `warp_sums` must
@@ -229,8 +245,16 @@ struct tn_plan {
 };
 
 namespace tn {
+// Internal apply flag: combine rows by byte-wise maximum (HyperLogLog
+// registers) instead of OR; no initialisation.
+constexpr uint32_t kApplyMax = 1u << 16;
 // Launch the column-slab streaming kernel for a list of (plan, matrix) jobs.
 tn_status apply_jobs(const tn_plan *const *plans, uint64_t *const *S, const uint32_t *ncols,
                      const uint32_t *const *src, int64_t *const *t_last, uint32_t count, uint32_t flags,
                      cudaStream_t stream);
+// Reversed copy of an event sequence (Section 3.4): event m-1-e becomes event e,
+// t -> ~t; with `turn` the endpoints are swapped (directed events).  The three
+// arrays come from the stream-ordered allocator; the caller frees them.
+tn_status reversed_events(const uint32_t *u, const uint32_t *v, const int64_t *t, uint64_t m, bool turn,
+                          uint32_t **ru, uint32_t **rv, int64_t **rt, cudaStream_t st);
 }  // namespace tn
