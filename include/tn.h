@@ -356,15 +356,20 @@ tn_status tn_error_stats_compute(const uint32_t *est, const uint32_t *exact, uin
 
 /* ---------------------------------------------------------------------------
  * tn_hash_estimate_noalloc -- the same fusion as tn_hash_estimate (same
- * arguments, same result bit for bit) for callers that must not allocate.
- * The paper has no counterpart to this entry point: it only changes where the
- * scratch lives.
+ * arguments, same result bit for bit) for callers that cannot allocate device
+ * memory while they run: code that executes inside another framework's memory
+ * pool or budget (where a cudaMalloc or a stream-ordered allocation would go
+ * around the owner's accounting or fail once the budget is reserved), and
+ * latency-bound loops where an allocation could synchronise the device or
+ * stall.  The paper has no counterpart to this entry point: it only changes
+ * where the scratch lives.
  *
  * It allocates nothing: no cudaMalloc / cudaFree / stream-ordered allocator or
  * allocating library call.  Its scratch is one fixed device array of
  * TN_NOALLOC_SCRATCH_BYTES bytes per device, owned by the library (static
- * storage of the library's module), whose address is looked up once per
- * device on the first call:
+ * storage of the library's module, held on every GPU that loads the library
+ * until the process exits), whose address is looked up once per device on the
+ * first call made with that device current:
  *   - a 4-byte flag for the source-id check, cleared on the stream before
  *     every validating call;
  *   - the per-CTA fusion tables when R * k exceeds the 200 KiB shared-memory

@@ -361,9 +361,12 @@ extern "C" tn_status tn_hash_estimate(const uint64_t *P, uint32_t R, uint32_t k,
 }
 
 // ---------------- fusion without allocation ----------------
-// Same kernels as tn_hash_estimate; the source-check flag and the per-CTA
-// tables of the global-table path live in one fixed device array of this
-// module instead of the stream-ordered allocator.  Bytes [0, 4) hold the
+// For callers that cannot allocate device memory during a call (code inside
+// another framework's memory budget, latency-bound loops).  Same kernels as
+// tn_hash_estimate; the source-check flag and the per-CTA tables of the
+// global-table path live in one fixed device array of this module instead of
+// the stream-ordered allocator.  Host code never uses the array's name as an
+// address: the address comes from cudaGetSymbolAddress, per device.  Bytes [0, 4) hold the
 // flag, the tables start at byte 256.
 #include <mutex>
 

@@ -1,5 +1,7 @@
 """tn_hash_estimate_noalloc against tn_hash_estimate (needs a GPU: -m gpu).
 
+The no-alloc variant serves callers that cannot allocate device memory during
+a call (code inside another framework's memory budget, latency-bound loops).
 The no-alloc entry point keeps its scratch in one fixed device array, so each
 case calls it twice in a row and checks both results against the allocating
 entry point on the same inputs: a first call that leaves stale scratch behind
