@@ -43,6 +43,8 @@ WORKLOADS = {
                         "integer seconds: large tie groups)", kind="bursty", n=500_000, m=100_000_000, seed=3),
     "hashed": dict(desc="hashed estimate n=1000000 m=100000000 activity-driven, k=16384, R=8, 65536 sampled sources",
                    kind="hashed", n=1_000_000, m=100_000_000, seed=4, k=16384, R=8, nsrc=65536),
+    "er-sweep": dict(desc="sweep: ER G(n, 2/n) with Poisson link activity, n in {100..10000}, m = 1e4..1e8; "
+                          "hashed estimate with n_s = 0.3 n, K = 5 against exact sizes", kind="sweep", n=0, m=0, seed=6),
     "serving": dict(desc="serving: Poisson arrivals 200 req/s, n log-uniform [1e3,1e5], m log-uniform [1e4,1e7], "
                          "uniform endpoints, 4 incremental batches per job", kind="serving", n=0, m=0, seed=5),
 }
@@ -63,6 +65,7 @@ def parse_args():
     ap.add_argument("--autotune", choices=["auto", "on", "off"], default="auto",
                     help="pick plan options with tn_autotune before timing (auto: on for bursty and hashed)")
     ap.add_argument("--tune-sample", type=int, default=2_000_000, help="events the autotuner times")
+    ap.add_argument("--sweep-max-m", type=float, default=1e8, help="er-sweep: largest number of events")
     ap.add_argument("--jobs", type=int, default=200, help="serving: number of jobs")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
     ap.add_argument("--max-active", type=int, default=16, help="serving: jobs resident at once")
@@ -496,6 +499,76 @@ def run_hashed(args, w, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def slab_for(n):
+    """Widest even slab (at most 16 words) that still gives 16 CTAs, at least 2 words."""
+    import paper_2307_04890_gb300 as tn
+    sw = min(tn.tn_row_words(n) // 16, 16) & ~1
+    return max(sw, 2)
+
+
+def run_sweep(args, w, rank, world, local_rank):
+    """The synthetic experiments of Sections 3.5 and 4.4: ER G(n, 2/n) with an
+    independent Poisson process per link.  For every (n, m): exact out-sizes
+    (component matrix) and hashed estimates (n_s = 0.3 n super-nodes, K = 5
+    replicas, all n sources), their Earth-Mover (W1) distance and relative
+    error, the GPU time of each (schedule + apply + sizes / hash + proxies +
+    fusion) and the memory of the matrices."""
+    import torch
+    import paper_2307_04890_gb300 as tn
+    from paper_2307_04890_gb300 import synth
+    from paper_2307_04890_gb300.build import build_library
+
+    build_library()
+    tn.load_library()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    K = 5
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    points = []
+    mmax = int(args.sweep_max_m)
+    for n in (100, 200, 500, 1000, 2000, 5000, 10000):
+        m = 10_000
+        while m <= mmax:
+            u, v, t = synth.er_poisson(n, m, seed=w["seed"] + 1000 * rank + n)
+            du = torch.from_numpy(u.view(np.int32)).to(dev)
+            dv = torch.from_numpy(v.view(np.int32)).to(dev)
+            dt = torch.from_numpy(t).to(dev)
+            k = max(1, int(0.3 * n))
+            e = [ev() for _ in range(4)]
+            torch.cuda.synchronize()
+            e[0].record()
+            plan = tn.Plan(du, dv, dt, n, slab_words=slab_for(n))
+            S = plan.apply(None, init=True)
+            exact, _, _ = tn.tn_out_sizes(S, n, n)
+            e[1].record()
+            e[2].record()
+            H, pu, pv = tn.tn_hash_proxy(du, dv, n, k, K, w["seed"])
+            plans = [tn.Plan(pu[j].contiguous(), pv[j].contiguous(), dt, k, slab_words=slab_for(k)) for j in range(K)]
+            P = torch.empty((K, k, tn.tn_row_words(k)), dtype=torch.int64, device=dev)
+            tn.tn_plan_apply_batch(plans, [P[j] for j in range(K)])
+            est = tn.tn_hash_estimate(P, K, k, H, n)
+            e[3].record()
+            err = tn.tn_error_stats(est, exact, n)
+            ex = exact.cpu().numpy().view(np.uint32)
+            points.append({"n": n, "m": m, "emd_w1": err["w1"], "mean_rel_error": err["mean_rel"],
+                           "max_rel_error": err["max_rel"], "mean_exact_size": float(ex.mean()),
+                           "exact_ms": e[0].elapsed_time(e[1]), "hashed_ms": e[2].elapsed_time(e[3]),
+                           "relative_time": e[2].elapsed_time(e[3]) / max(e[0].elapsed_time(e[1]), 1e-9),
+                           "relative_memory": K * k * ((k + 63) // 64) / (n * ((n + 63) // 64))})
+            for p_ in plans:
+                p_.destroy()
+            plan.destroy()
+            del S, P, H, pu, pv, du, dv, dt
+            m *= 10
+    result = {"metric": "hashed estimate accuracy and cost against the exact matrix (ER sweep)",
+              "value": float(np.mean([q["emd_w1"] for q in points])), "unit": "mean W1 over the sweep",
+              "n_gpus": world, "steps": len(points), "warmup": 0, "ms_per_step": float(np.mean([q["exact_ms"] + q["hashed_ms"] for q in points])),
+              "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+              "data": "synthetic", "config": {"workload": w["desc"], "n_s": "0.3 n", "K": K}, "sweep": points}
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+
+
 def main():
     args = parse_args()
     w = WORKLOADS[args.workload]
@@ -507,6 +580,13 @@ def main():
         return
     if w["kind"] == "hashed" and args.impl == "ours":
         run_hashed(args, w, rank, world, local_rank)
+        return
+    if w["kind"] == "sweep":
+        if args.impl == "ours":
+            run_sweep(args, w, rank, world, local_rank)
+        elif rank == 0:
+            print(json.dumps({"impl": "reference", "unavailable": "the sweep compares two GPU paths; its oracle "
+                              "counterpart is the parity suite"}), flush=True)
         return
     if args.impl == "reference":
         run_reference(args, w, rank, world)
