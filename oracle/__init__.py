@@ -14,6 +14,8 @@ arrays.  Functions cite the paper passage they follow:
   (footnote to Section 3.1: only the receiver's row is updated).
 * ``hll_singleton`` / ``hll_sketches`` / ``hll_estimate`` -- HyperLogLog
   sketches of the components and their size estimates (Section 3.4).
+* ``grow_matrix``       -- node growth: a new row and column, False except the
+  diagonal (Section 3.5, advantages and limitations of the matrix method).
 * ``si_reach``          -- the deterministic SI process (Section 1).
 * ``column_counts`` / ``row_counts`` / ``argmax`` -- component sizes
   (Section 3.1, eq. for the mean size s_t in Section 3.3).
@@ -74,6 +76,9 @@ def _load():
         lib.tnref_apply_events_reversed.restype = ctypes.c_int
         lib.tnref_apply_events_directed.argtypes = lib.tnref_apply_events.argtypes
         lib.tnref_apply_events_directed.restype = ctypes.c_int
+        lib.tnref_grow_matrix.argtypes = [_u64p, ctypes.c_uint32, ctypes.c_uint64,
+                                          _u64p, ctypes.c_uint32, ctypes.c_uint64]
+        lib.tnref_grow_matrix.restype = ctypes.c_int
         lib.tnref_si_reach_directed.argtypes = [_u32p, _u32p, _i64p, ctypes.c_uint64, ctypes.c_uint32,
                                                 ctypes.c_uint32, _u8p]
         lib.tnref_hll_singleton.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
@@ -201,6 +206,17 @@ def si_reach(u, v, t, n, source) -> np.ndarray:
     out = np.zeros(n, dtype=np.uint8)
     _check(_load().tnref_si_reach(u, v, t, len(u), n, source, out))
     return out.astype(bool)
+
+
+def grow_matrix(S: np.ndarray, n_old: int, n_new: int) -> np.ndarray:
+    """Node growth (Section 3.5): the n_old x n_old matrix S extended to n_new
+    nodes, each new node a new row and column that is False except on the
+    diagonal.  Returns a new n_new x words(n_new) matrix."""
+    S = np.ascontiguousarray(S, dtype=np.uint64)
+    assert S.shape[0] == n_old
+    out = np.zeros((n_new, max(1, words(n_new))), dtype=np.uint64)
+    _check(_load().tnref_grow_matrix(S.reshape(-1), n_old, S.shape[1], out.reshape(-1), n_new, out.shape[1]))
+    return out
 
 
 def column_counts(S: np.ndarray, ncols: int) -> np.ndarray:

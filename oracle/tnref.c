@@ -310,6 +310,29 @@ int tnref_si_reach(const uint32_t *u, const uint32_t *v, const int64_t *t,
 }
 
 /* ---------------------------------------------------------------------------
+ * Node growth (Section 3.5, advantages and limitations of the matrix method):
+ * a node that joins the network adds one row and one column, all "False"
+ * except the diagonal element.  S_old is n_old x n_old (row stride w_old
+ * words), S_new is n_new x n_new (row stride w_new words), n_new >= n_old:
+ *   S_new[i][j] = S_old[i][j]  for i, j < n_old,
+ *   S_new[i][i] = 1            for n_old <= i < n_new,
+ *   every other bit 0.
+ * ------------------------------------------------------------------------- */
+int tnref_grow_matrix(const uint64_t *S_old, uint32_t n_old, uint64_t w_old,
+                      uint64_t *S_new, uint32_t n_new, uint64_t w_new)
+{
+    if (n_new < n_old || 64 * w_old < n_old || 64 * w_new < n_new) return TNREF_EINVAL;
+    memset(S_new, 0, (size_t)n_new * w_new * sizeof(uint64_t));
+    for (uint32_t i = 0; i < n_old; ++i)
+        for (uint32_t j = 0; j < n_old; ++j)
+            if ((S_old[(uint64_t)i * w_old + j / 64] >> (j % 64)) & 1u)
+                S_new[(uint64_t)i * w_new + j / 64] |= 1ull << (j % 64);
+    for (uint32_t i = n_old; i < n_new; ++i)
+        S_new[(uint64_t)i * w_new + i / 64] |= 1ull << (i % 64);
+    return TNREF_OK;
+}
+
+/* ---------------------------------------------------------------------------
  * Component sizes (Section 3, "count the number of ones in the corresponding
  * column"; eq. for s_t: row sums and column sums have the same total).
  * out[c] = number of rows with bit c set (out-component size of column c);

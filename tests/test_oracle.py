@@ -176,6 +176,76 @@ def test_incremental_equals_one_shot_and_monotone():
     assert np.array_equal(S, full)
 
 
+# --------------------------------------------------------------------------
+# node growth (Section 3.5: a new node is a new row and column, False except
+# on the diagonal)
+# --------------------------------------------------------------------------
+def _pack(B):
+    B = np.asarray(B, dtype=bool)
+    W = max(1, oracle.words(B.shape[1]))
+    out = np.zeros((B.shape[0], W), dtype=np.uint64)
+    for i, j in zip(*np.nonzero(B)):
+        out[i, j // 64] |= np.uint64(1) << np.uint64(j % 64)
+    return out
+
+
+def test_grow_hand_example():
+    old = [[1, 1, 0],
+           [0, 1, 0],
+           [0, 1, 1]]
+    want = [[1, 1, 0, 0, 0],
+            [0, 1, 0, 0, 0],
+            [0, 1, 1, 0, 0],
+            [0, 0, 0, 1, 0],
+            [0, 0, 0, 0, 1]]
+    G = oracle.grow_matrix(_pack(old), 3, 5)
+    assert np.array_equal(oracle.to_bool(G, 5), np.array(want, dtype=bool))
+
+
+@pytest.mark.parametrize("n_old,n_new", [(0, 4), (5, 5), (64, 65), (60, 130)])
+def test_grow_identity_stays_identity(n_old, n_new):
+    G = oracle.grow_matrix(oracle.init_sources(n_old) if n_old else np.zeros((0, 1), np.uint64), n_old, n_new)
+    assert np.array_equal(oracle.to_bool(G, n_new), np.eye(n_new, dtype=bool))
+
+
+@pytest.mark.parametrize("seed,n_old,n_new", [(0, 60, 130), (1, 10, 11), (2, 128, 200)])
+def test_grow_then_stream_matches_si_on_the_larger_network(seed, n_old, n_new):
+    """Nodes that join after the first batch: growing the matrix and streaming
+    the second batch gives every source's SI reach over all events."""
+    rng = np.random.default_rng(seed)
+    m1, m2 = 3 * n_old, 3 * n_new
+    u1 = rng.integers(0, n_old, m1).astype(np.uint32)
+    v1 = rng.integers(0, n_old, m1).astype(np.uint32)
+    t1 = np.sort(rng.integers(0, 50, m1)).astype(np.int64)
+    u2 = rng.integers(0, n_new, m2).astype(np.uint32)
+    v2 = rng.integers(0, n_new, m2).astype(np.uint32)
+    t2 = np.sort(rng.integers(50, 100, m2)).astype(np.int64)
+    S = oracle.grow_matrix(oracle.component_matrix(u1, v1, t1, n_old), n_old, n_new)
+    oracle.apply_events(u2, v2, t2, n_new, S)
+    B = oracle.to_bool(S, n_new)
+    u, v, t = np.concatenate([u1, u2]), np.concatenate([v1, v2]), np.concatenate([t1, t2])
+    for j in range(n_new):
+        assert np.array_equal(B[:, j], oracle.si_reach(u, v, t, n_new, j)), j
+
+
+def test_grow_rejects_shrinking():
+    with pytest.raises(oracle.OracleError):
+        oracle.grow_matrix(oracle.init_sources(5), 5, 4)
+
+
+def test_split_group_needs_the_whole_group():
+    """A timestamp group is one snapshot: applying its two halves as separate
+    batches (what an incremental caller would do without carrying the group)
+    lets a path run through it, which the whole group does not."""
+    u, v, t = _arrays([(0, 1, 1), (1, 2, 1)])
+    whole = oracle.to_bool(oracle.component_matrix(u, v, t, 3), 3)
+    assert sorted(np.flatnonzero(whole[:, 0]).tolist()) == [0, 1]
+    S = oracle.init_sources(3)
+    oracle.apply_events(u[:1], v[:1], t[:1], 3, S)
+    oracle.apply_events(u[1:], v[1:], t[1:], 3, S)
+    assert sorted(np.flatnonzero(oracle.to_bool(S, 3)[:, 0]).tolist()) == [0, 1, 2]
+
+
 def test_order_inside_groups_is_irrelevant():
     (u, v, t), n = _cfg_small(9)
     rng = np.random.default_rng(1)
