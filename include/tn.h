@@ -87,6 +87,9 @@ typedef int32_t tn_status;
                                TN_INIT_IDENTITY and t_last == NULL
                                (it is not a streaming mode).  Scratch: 16 bytes per event. */
 
+#define TN_GROUP_END 8u       /* tn_online_push only: the batch's last timestamp group is
+                               complete (no later batch continues it) */
+
 /* Human-readable name of a status code (static storage, never NULL). */
 const char *tn_status_string(tn_status status);
 
@@ -453,6 +456,102 @@ tn_status tn_server_get_stats(tn_server *server, tn_server_stats *stats);
 /* Finishes every queued and running job, then stops the worker and frees the
  * server (records not yet polled are dropped). */
 tn_status tn_server_destroy(tn_server *server);
+
+/* ---------------------------------------------------------------------------
+ * Node growth (Section 3.5, advantages and limitations of the matrix method:
+ * a node that joins the network adds a row and a column to the component
+ * matrix, "False" except the diagonal element).
+ *
+ * tn_grow_matrix -- S_new (n_new x n_new, layout above) receives S_old
+ * (n_old x n_old) in its first n_old rows and columns, with bits of columns
+ * >= n_old cleared, and the identity on the new nodes:
+ *   S_new[i][j] = S_old[i][j] for i, j < n_old;  S_new[i][i] = 1 for i >= n_old;
+ *   every other bit 0.
+ *   S_old  uint64[n_old * tn_row_words(n_old)], may be NULL when n_old == 0.
+ *   S_new  uint64[n_new * tn_row_words(n_new)]; either disjoint from S_old, or
+ *          equal to it when tn_row_words(n_new) == tn_row_words(n_old) (in
+ *          place: the buffer must already hold n_new rows; only the new rows
+ *          and the new columns of the old rows are written).
+ * TN_EINVAL for n_new < n_old, n_new >= 2^30, partially overlapping buffers,
+ * an in-place call whose row stride would change, or a pointer that is not
+ * 16-byte aligned.  Asynchronous.
+ */
+tn_status tn_grow_matrix(const uint64_t *S_old, uint32_t n_old, uint64_t *S_new, uint32_t n_new,
+                         void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Online state (Section 3.5: one pass over the events, new events and new
+ * nodes processed as they arrive).  The object owns a component matrix on the
+ * device that starts as I_n and takes event batches in time order and node
+ * growth at any point between them.
+ *
+ * Timestamp groups may be split across batches.  A group is one snapshot
+ * (Section 2.1: adjacency needs dt > 0), so none of its events may be applied
+ * before all of them are known: every push holds back the events of the
+ * batch's last timestamp ("pending") and applies them with the next batch,
+ * whose first events may continue the same group, unless the push carries
+ * TN_GROUP_END.  After a push, S therefore holds every pushed event with a
+ * timestamp below the pending one; after tn_online_flush (or a push with
+ * TN_GROUP_END) it holds all of them, and the next batch must start at a
+ * strictly later timestamp.  The result equals tn_component_matrix over the
+ * concatenation of the batches (on the grown matrix, where nodes were added).
+ *
+ * All calls of one object must come from one host thread at a time, on one
+ * device (the one current at create); the matrix and the held-back events
+ * live in the stream-ordered pool, and `stream` may differ between calls only
+ * if the caller orders those streams.
+ */
+typedef struct tn_online tn_online;
+
+typedef struct tn_online_state {
+    uint64_t *S;             /* device matrix, n x row_words words; moves when a
+                                tn_online_grow changes the row stride */
+    uint32_t n;              /* current number of nodes */
+    uint32_t has_applied;    /* 1 once any event has been applied to S */
+    uint64_t row_words;      /* tn_row_words(n) */
+    uint64_t pending_events; /* events held back (timestamp pending_t) */
+    int64_t pending_t;
+    int64_t t_applied;       /* last timestamp applied to S (if has_applied) */
+    uint64_t applied_events; /* events applied to S so far */
+    uint64_t batches;        /* pushes accepted */
+} tn_online_state;
+
+/* Creates the state for n nodes (S <- I_n, Algorithm 1).  opt as for
+ * tn_plan_create (NULL = defaults; opt->directed selects directed events).
+ * TN_EINVAL for n == 0, n >= 2^30 or bad options. */
+tn_status tn_online_create(uint32_t n, const tn_plan_options *opt, void *stream, tn_online **online);
+
+/* Pushes a batch: u, v uint32[m] (device, < current n), t int64[m] (device,
+ * non-decreasing).  Its first timestamp must be >= the pending timestamp when
+ * events are pending (equal: the batch continues the pending group), else
+ * > the last applied timestamp.  flags: 0 or TN_GROUP_END.  m == 0 is allowed
+ * (with TN_GROUP_END it applies the pending group).  Validating and
+ * synchronous up to the scheduling of the complete groups (TN_ERANGE,
+ * TN_EORDER leave the state unchanged); the matrix update runs on `stream`
+ * after the call returns and may be read by later work on that stream.  A
+ * device error of an applied batch is returned by the next call on the
+ * object.  The caller may reuse u, v, t once the call returns. */
+tn_status tn_online_push(tn_online *online, const uint32_t *u, const uint32_t *v, const int64_t *t,
+                         uint64_t m, uint32_t flags, void *stream);
+
+/* Applies the pending group (same as a push of no events with TN_GROUP_END). */
+tn_status tn_online_flush(tn_online *online, void *stream);
+
+/* Adds nodes n .. n_new - 1 (tn_grow_matrix on the owned matrix; in place
+ * while the row stride stays, else into a new buffer).  Pending events stay
+ * pending; later batches may use the new ids.  TN_EINVAL for n_new < n. */
+tn_status tn_online_grow(tn_online *online, uint32_t n_new, void *stream);
+
+/* Waits for `stream` and returns the first device error of an applied batch
+ * (TN_OK if none); the error is sticky. */
+tn_status tn_online_status(tn_online *online, void *stream);
+
+/* Host-side snapshot of the state (no synchronisation). */
+tn_status tn_online_get_state(const tn_online *online, tn_online_state *state);
+
+/* Frees the object; its memory is returned on `stream` after the work already
+ * enqueued there. */
+tn_status tn_online_destroy(tn_online *online, void *stream);
 
 /* ---------------------------------------------------------------------------
  * HyperLogLog sketches of the components (Section 3.4).  Approximate: O(n s)

@@ -24,9 +24,9 @@ __all__ = [
     "tn_hash_proxy", "tn_hash_estimate", "tn_hash_estimate_noalloc", "tn_error_stats",
     "tn_out_component_sizes_host",
     "Plan", "tn_plan_apply_batch", "Server", "BatchGraph", "tn_autotune", "tn_selftest_wait_timeout",
-    "tn_hll_sketches", "tn_hll_estimate",
+    "tn_hll_sketches", "tn_hll_estimate", "tn_grow_matrix", "Online",
     "TN_OK", "TN_EINVAL", "TN_ERANGE", "TN_EORDER", "TN_ENOMEM", "TN_ECUDA", "TN_ETIMEOUT", "TN_ESCRATCH",
-    "TN_INIT_IDENTITY", "TN_REVERSE", "TN_DIRECTED",
+    "TN_INIT_IDENTITY", "TN_REVERSE", "TN_DIRECTED", "TN_GROUP_END",
 ]
 
 TN_OK, TN_EINVAL, TN_ERANGE, TN_EORDER, TN_ENOMEM, TN_ECUDA, TN_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
@@ -34,6 +34,7 @@ TN_ESCRATCH = -7
 TN_INIT_IDENTITY = 1
 TN_REVERSE = 2
 TN_DIRECTED = 4
+TN_GROUP_END = 8
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIBRARY_PATH = os.path.join(_HERE, "libtn.so")
@@ -137,6 +138,14 @@ def load_library(path: str | None = None):
         "tn_server_get_stats": ([vp, ctypes.POINTER(_ServerStats)], i32),
         "tn_server_destroy": ([vp], i32),
         "tn_out_component_sizes_host": ([vp, vp, vp, u64, u32, vp, vp, vp], i32),
+        "tn_grow_matrix": ([vp, u32, vp, u32, vp], i32),
+        "tn_online_create": ([u32, ctypes.POINTER(_Options), vp, ctypes.POINTER(vp)], i32),
+        "tn_online_push": ([vp, vp, vp, vp, u64, u32, vp], i32),
+        "tn_online_flush": ([vp, vp], i32),
+        "tn_online_grow": ([vp, u32, vp], i32),
+        "tn_online_status": ([vp, vp], i32),
+        "tn_online_get_state": ([vp, ctypes.POINTER(_OnlineState)], i32),
+        "tn_online_destroy": ([vp, vp], i32),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(lib, name)
@@ -351,6 +360,12 @@ def tn_out_component_sizes_host_ptrs(u_ptr: int, v_ptr: int, t_ptr: int, m: int,
            "tn_out_component_sizes_host")
 
 
+class _OnlineState(ctypes.Structure):
+    _fields_ = [("S", ctypes.c_void_p), ("n", ctypes.c_uint32), ("has_applied", ctypes.c_uint32),
+                ("row_words", ctypes.c_uint64), ("pending_events", ctypes.c_uint64), ("pending_t", ctypes.c_int64),
+                ("t_applied", ctypes.c_int64), ("applied_events", ctypes.c_uint64), ("batches", ctypes.c_uint64)]
+
+
 class Plan:
     """A validated, scheduled event batch (tn_plan_create / tn_plan_apply)."""
 
@@ -556,3 +571,89 @@ def tn_hll_estimate(R, n: int, p: int, stream=None):
     est = torch.empty(n, dtype=torch.float64, device=R.device)
     _check(lib.tn_hll_estimate(_ptr(R), n, p, _ptr(est), _stream(stream)), "tn_hll_estimate")
     return est
+
+
+def tn_grow_matrix(S, n_old: int, n_new: int, out=None, stream=None):
+    """Node growth (Section 3.5): S (n_old x n_old) extended by new rows and
+    columns that are False except the diagonal.  Writes into ``out`` (a new
+    n_new x tn_row_words(n_new) tensor when None; ``out is S`` grows in place,
+    which needs an unchanged row stride and room for n_new rows)."""
+    lib = load_library()
+    torch = _torch()
+    S = _matrix(S, S.shape[0], n_old, S.device) if n_old else S
+    if out is None:
+        out = torch.empty((n_new, tn_row_words(n_new)), dtype=torch.int64, device=S.device)
+    _dev(out, ("int64", "uint64"), "out")
+    if out.shape[1] != tn_row_words(n_new) or out.shape[0] < n_new:
+        raise ValueError("out must have tn_row_words(n_new) columns and at least n_new rows")
+    _check(lib.tn_grow_matrix(_ptr(S) if n_old else None, n_old, _ptr(out), n_new, _stream(stream)),
+           "tn_grow_matrix")
+    return out
+
+
+class _DeviceView:
+    """Exposes library-owned device memory to torch without a copy."""
+
+    def __init__(self, ptr: int, shape):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": "<i8", "data": (ptr, False),
+                                         "version": 3, "strides": None}
+
+
+class Online:
+    """Online component matrix (tn_online_*, Section 3.5): batches of device
+    events in time order, timestamp groups may be split across batches, nodes
+    may be added between batches."""
+
+    def __init__(self, n: int, window_events: int = 0, slab_words: int = 0, smem_rows: int = 0,
+                 directed: bool = False, stream=None):
+        lib = load_library()
+        opt = _Options(window_events, slab_words, smem_rows, 1 if directed else 0)
+        h = ctypes.c_void_p()
+        _check(lib.tn_online_create(n, ctypes.byref(opt), _stream(stream), ctypes.byref(h)), "tn_online_create")
+        self._h = h
+
+    def push(self, u, v, t, group_end: bool = False, stream=None):
+        """Applies every complete timestamp group; the batch's last group stays
+        pending unless ``group_end``."""
+        m = _events(u, v, t)
+        _check(load_library().tn_online_push(self._h, _ptr(u), _ptr(v), _ptr(t), m,
+                                             TN_GROUP_END if group_end else 0, _stream(stream)),
+               "tn_online_push")
+
+    def flush(self, stream=None):
+        _check(load_library().tn_online_flush(self._h, _stream(stream)), "tn_online_flush")
+
+    def grow(self, n_new: int, stream=None):
+        _check(load_library().tn_online_grow(self._h, n_new, _stream(stream)), "tn_online_grow")
+
+    def status(self, stream=None) -> int:
+        return load_library().tn_online_status(self._h, _stream(stream))
+
+    def state(self) -> dict:
+        st = _OnlineState()
+        _check(load_library().tn_online_get_state(self._h, ctypes.byref(st)), "tn_online_get_state")
+        return {name: getattr(st, name) for name, _ in _OnlineState._fields_}
+
+    def matrix(self):
+        """The current matrix as an int64 [n, tn_row_words(n)] tensor that
+        aliases the library's buffer (valid until the next grow or close)."""
+        torch = _torch()
+        st = self.state()
+        return torch.as_tensor(_DeviceView(st["S"], (st["n"], st["row_words"])), device="cuda")
+
+    def close(self, stream=None):
+        if self._h:
+            _check(load_library().tn_online_destroy(self._h, _stream(stream)), "tn_online_destroy")
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
