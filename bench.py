@@ -30,6 +30,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "events/s and bit-updates/s (n·m/time) at 1 GB300; achieved HBM GB/s vs peak"
+ONLINE_METRIC = "events/s through the online state (batches that split timestamp groups)"
 PROFILE_SUMMARIES = {"activity": "stream_kernel_activity_n1e5_m1e7.txt",
                      "bursty": "stream_kernel_bursty_n5e5_m1e8.txt"}
 KERNEL_SOURCES = ["paper_2307_04890_gb300/csrc/tn_apply.cu", "paper_2307_04890_gb300/csrc/tn_internal.cuh"]
@@ -45,6 +46,9 @@ WORKLOADS = {
                    kind="hashed", n=1_000_000, m=100_000_000, seed=4, k=16384, R=8, nsrc=65536),
     "er-sweep": dict(desc="sweep: ER G(n, 2/n) with Poisson link activity, n in {100..10000}, m = 1e4..1e8; "
                           "hashed estimate with n_s = 0.3 n, K = 5 against exact sizes", kind="sweep", n=0, m=0, seed=6),
+    "online": dict(desc="online: the activity-driven n=100000 m=10000000 stream pushed in 16 batches cut at seeded "
+                        "points, 7 of them inside timestamp groups, plus node growth 100000 -> 102048",
+                   kind="online", n=100_000, m=10_000_000, seed=2, batches=16, grow_to=102_048),
     "serving": dict(desc="serving: Poisson arrivals 200 req/s, n log-uniform [1e3,1e5], m log-uniform [1e4,1e7], "
                          "uniform endpoints, 4 incremental batches per job", kind="serving", n=0, m=0, seed=5),
 }
@@ -75,7 +79,7 @@ def parse_args():
 def make_events(w, rank=0):
     from paper_2307_04890_gb300 import synth
     seed = replica_seed(w, rank)
-    if w["kind"] in ("activity", "hashed"):
+    if w["kind"] in ("activity", "hashed", "online"):
         return synth.activity_driven(w["n"], w["m"], seed=seed)
     if w["kind"] == "bursty":
         return synth.powerlaw_bursty(w["n"], w["m"], seed=seed)
@@ -283,14 +287,17 @@ def run_reference(args, w, rank, world):
             times.append(dt)
     mean = sum(times) / len(times)
     value = n * ms / mean
+    metric, unit = METRIC, "bit-updates/s"
+    if w["kind"] == "online":  # the online arm reports events/s
+        value, metric, unit = ms / mean, ONLINE_METRIC, "events/s"
     sample = f"first {ms} of {w['m']} events (group boundary), all {n} columns, one thread"
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "bit-updates/s", "n_gpus": world,
+    line = {"impl": "reference", "metric": metric, "value": value, "unit": unit, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": w["desc"], "n": n, "m": w["m"]},
             "events_per_s": ms / mean,
-            "cpu_baseline": {"value": value, "unit": "bit-updates/s", "cores": 1, "kind": "oracle", "sample": sample},
-            "e2e": {"value": value, "unit": "bit-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "cpu_baseline": {"value": value, "unit": unit, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
@@ -499,6 +506,142 @@ def run_hashed(args, w, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def run_online(args, w, rank, world, local_rank):
+    """The online state (tn_online_*): one step pushes the whole stream in
+    batches cut at arbitrary points, flushes and takes the out-sizes.  Beside
+    it: the same step with every batch copied from pinned host memory (e2e),
+    and the one-shot step over the same events (schedule + init + apply +
+    sizes), which must give the same matrix.  Node growth is timed on its own:
+    the reallocating growth of the final matrix to more nodes (an HBM copy)."""
+    import torch
+    import paper_2307_04890_gb300 as tn
+    from paper_2307_04890_gb300.build import build_library
+
+    build_library()
+    tn.load_library()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    n, m, B = w["n"], w["m"], w["batches"]
+    u, v, t = make_events(w, rank)
+    du = torch.from_numpy(u.view(np.int32)).to(dev)
+    dv = torch.from_numpy(v.view(np.int32)).to(dev)
+    dt = torch.from_numpy(t).to(dev)
+    hu = torch.from_numpy(u.view(np.int32)).pin_memory()
+    hv = torch.from_numpy(v.view(np.int32)).pin_memory()
+    ht = torch.from_numpy(t).pin_memory()
+    rng = np.random.default_rng(replica_seed(w, rank))
+    # half of the cuts inside timestamp groups (between two events of equal t), half anywhere
+    inside = np.flatnonzero(t[1:] == t[:-1]) + 1
+    picks = rng.choice(inside, min(len(inside), (B - 1) // 2), replace=False) if len(inside) else np.array([], int)
+    rest = rng.choice(np.setdiff1d(np.arange(1, m), picks), B - 1 - len(picks), replace=False)
+    cuts = np.r_[0, np.sort(np.r_[picks, rest]), m].astype(np.int64)
+    split = int(sum(1 for c in cuts[1:-1] if t[c - 1] == t[c]))
+    stream = torch.cuda.current_stream(dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def online_step():
+        on = tn.Online(n)
+        for a, b in zip(cuts[:-1], cuts[1:]):
+            on.push(du[a:b], dv[a:b], dt[a:b])
+        on.flush()
+        out, _, am = tn.tn_out_sizes(on.matrix(), n, n, argmax=True)
+        return on, out, am
+
+    def online_e2e_step():
+        on = tn.Online(n)
+        for a, b in zip(cuts[:-1], cuts[1:]):
+            on.push(hu[a:b].to(dev, non_blocking=True), hv[a:b].to(dev, non_blocking=True),
+                    ht[a:b].to(dev, non_blocking=True))
+        on.flush()
+        out, _, am = tn.tn_out_sizes(on.matrix(), n, n, argmax=True)
+        return on, out.cpu(), am.cpu()
+
+    def one_shot_step():
+        plan = tn.Plan(du, dv, dt, n)
+        S = plan.apply(None, init=True)
+        out, _, am = tn.tn_out_sizes(S, n, n, argmax=True)
+        plan.destroy()
+        return S, out, am
+
+    def release(r):
+        if isinstance(r[0], tn.Online):
+            r[0].close()
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            r = fn()
+            torch.cuda.synchronize()
+            release(r)
+        if dist:
+            dist.barrier()
+        e0, e1 = ev(), ev()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for i in range(args.steps):
+            r = fn()
+            if i < args.steps - 1:
+                release(r)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return job_max_ms(e0.elapsed_time(e1), dist, dev) / args.steps, r
+
+    launches0 = tn.tn_kernel_launches()
+    with ClockSampler(torch.cuda.current_device()) as clocks:
+        online_ms, (on, out_on, am_on) = timed(online_step)
+    launches = (tn.tn_kernel_launches() - launches0) // args.steps
+    e2e_ms, (on_e2e, out_e2e, _) = timed(online_e2e_step)
+    e2e_ok = bool(torch.equal(out_e2e, out_on.cpu()))
+    on_e2e.close()
+    shot_ms, (S_ref, out_ref, am_ref) = timed(one_shot_step)
+    identical = bool(torch.equal(on.matrix(), S_ref) and torch.equal(out_on, out_ref) and
+                     int(am_on.item()) == int(am_ref.item()))
+    del S_ref
+    # node growth into a new buffer (the row stride grows), timed alone
+    n2 = w["grow_to"]
+    S0 = on.matrix()
+    G = torch.empty((n2, tn.tn_row_words(n2)), dtype=torch.int64, device=dev)
+    for _ in range(3):
+        tn.tn_grow_matrix(S0, n, n2, out=G)
+    reps = 10
+    e0, e1 = ev(), ev()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        tn.tn_grow_matrix(S0, n, n2, out=G)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    grow_ms = e0.elapsed_time(e1) / reps
+    grow_bytes = n * tn.tn_row_words(n) * 8 + n2 * tn.tn_row_words(n2) * 8
+    grown_ok = bool(torch.equal(G[:n, : tn.tn_row_words(n)], S0) and
+                    int(tn.tn_out_sizes(G, n2, n2)[0][n:].sum().item()) == n2 - n)
+    on.close()
+    peak, peak_kind = measured_peaks()
+    result = {"metric": ONLINE_METRIC, "value": world * m / (online_ms * 1e-3), "unit": "events/s",
+              "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": online_ms,
+              "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+              "config": {"workload": w["desc"], "n": n, "m": m, "batches": B, "cuts_inside_a_group": split,
+                         "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                         "l2": "inputs larger than L2 (S 1.25 GB, events 160 MB)"},
+              "e2e": {"value": world * m / (e2e_ms * 1e-3), "unit": "events/s", "h2d_bytes_per_step": m * 16,
+                      "d2h_bytes_per_step": n * 4 + 4, "ms_per_step": e2e_ms, "identical": e2e_ok},
+              "one_shot_ms": shot_ms, "online_over_one_shot": online_ms / shot_ms,
+              "identical_to_one_shot": identical,
+              "roofline": {"bound": "hbm", "kernel": "grow_kernel (growth %d -> %d nodes into a new buffer)" % (n, n2),
+                           "achieved": grow_bytes / (grow_ms * 1e-3) / 1e9, "peak": peak,
+                           "peak_source": f"{peak_kind} MEASURED_PEAKS hbm_gbs", "unit": "GB/s",
+                           "frac": grow_bytes / (grow_ms * 1e-3) / 1e9 / peak, "traffic": None,
+                           "algorithmic_bytes_per_launch": grow_bytes, "kernel_ms": grow_ms, "correct": grown_ok},
+              "gpu_launches": launches, "clocks": clocks.summary()}
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
 def slab_for(n):
     """Widest even slab (at most 16 words) that still gives 16 CTAs, at least 2 words."""
     import paper_2307_04890_gb300 as tn
@@ -580,6 +723,9 @@ def main():
         return
     if w["kind"] == "hashed" and args.impl == "ours":
         run_hashed(args, w, rank, world, local_rank)
+        return
+    if w["kind"] == "online" and args.impl == "ours":
+        run_online(args, w, rank, world, local_rank)
         return
     if w["kind"] == "sweep":
         if args.impl == "ours":
