@@ -402,8 +402,10 @@ tn_status tn_hash_estimate_noalloc(const uint64_t *P, uint32_t R, uint32_t k, co
  * memory_budget, so jobs that arrive while others run join the device as soon
  * as a slot and memory free up.  Each admitted job runs on its own stream:
  * its batches are copied in, scheduled and applied in order to one matrix kept
- * on the device (S <- I first; each batch must start after the previous
- * one's last timestamp, checked on the device), then its out-sizes (and
+ * on the device (S <- I first; timestamps must not decrease across batches,
+ * checked on the device; a batch boundary that falls inside a timestamp group
+ * is moved at submit to the end of that group, so the group is applied whole
+ * with the following batch, Section 2.1), then its out-sizes (and
  * largest out-component) are copied to the caller's host buffers.  Jobs on
  * different streams overlap on the device.  Results are exactly those of
  * tn_out_component_sizes_host on the concatenated events.
@@ -438,8 +440,9 @@ tn_status tn_server_create(const tn_server_options *opt, tn_server **server);
 
 /* Queues job `job_id`: n nodes; HOST arrays u, v, t (pinned or pageable) of
  * batch_offsets[nbatches] events, batch b = [batch_offsets[b],
- * batch_offsets[b+1]) (batch_offsets[0] = 0, non-decreasing, each batch
- * < 2^30 events); out_sizes a HOST uint32[n], argmax a HOST uint32 or NULL.
+ * batch_offsets[b+1]) (batch_offsets[0] = 0, non-decreasing; a boundary
+ * inside a timestamp group moves to the group's end, and each batch must then
+ * hold < 2^30 events); out_sizes a HOST uint32[n], argmax a HOST uint32 or NULL.
  * The caller keeps every buffer alive until the job's record is returned by
  * tn_server_poll.  TN_ENOMEM if the job could never fit the budget. */
 tn_status tn_server_submit(tn_server *server, uint64_t job_id, uint32_t n, const uint32_t *u,

@@ -13,7 +13,8 @@
 //     batch is scheduled (tn_plan_create), and the batches are applied in
 //     order to the same S with the t_last order gate, followed by the
 //     out-sizes and the copy back.  Jobs on different streams overlap on the
-//     device;
+//     device.  A batch boundary inside a timestamp group is moved to the end
+//     of the group at submit, so each group is applied whole;
 //   * finished jobs release their memory and report timings through poll().
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -320,10 +321,25 @@ extern "C" tn_status tn_server_submit(tn_server *s, uint64_t job_id, uint32_t n,
     if (!s || n == 0 || n >= (1u << 30) || !batch_offsets || nbatches == 0 || !out_sizes) return TN_EINVAL;
     const uint64_t m = batch_offsets[nbatches];
     if (batch_offsets[0] != 0 || (m > 0 && (!u || !v || !t))) return TN_EINVAL;
+    for (uint32_t b = 0; b < nbatches; ++b)
+        if (batch_offsets[b + 1] < batch_offsets[b]) return TN_EINVAL;
+    std::vector<uint64_t> offs;
+    try {
+        offs.assign(batch_offsets, batch_offsets + nbatches + 1);
+    } catch (...) {
+        return TN_ENOMEM;
+    }
+    // A timestamp group is one snapshot (Section 2.1), so it must be applied
+    // whole: a batch boundary inside a group moves to the group's end, and the
+    // group is applied with the next batch (as the online state holds it back).
+    for (uint32_t b = 1; b < nbatches; ++b) {
+        uint64_t x = offs[b] > offs[b - 1] ? offs[b] : offs[b - 1];
+        while (x > 0 && x < m && t[x] == t[x - 1]) ++x;
+        offs[b] = x;
+    }
     uint64_t max_batch = 0;
     for (uint32_t b = 0; b < nbatches; ++b) {
-        if (batch_offsets[b + 1] < batch_offsets[b]) return TN_EINVAL;
-        const uint64_t mb = batch_offsets[b + 1] - batch_offsets[b];
+        const uint64_t mb = offs[b + 1] - offs[b];
         if (mb >= (1ull << 30)) return TN_EINVAL;
         if (mb > max_batch) max_batch = mb;
     }
@@ -334,7 +350,7 @@ extern "C" tn_status tn_server_submit(tn_server *s, uint64_t job_id, uint32_t n,
     j->hu = u;
     j->hv = v;
     j->ht = t;
-    j->offs.assign(batch_offsets, batch_offsets + nbatches + 1);
+    j->offs.swap(offs);
     j->h_out = out_sizes;
     j->h_argmax = argmax;
     j->bytes = job_bytes(n, m, max_batch);

@@ -118,3 +118,26 @@ def test_out_of_range_endpoint_is_reported():
         u = np.array([0, 5, 1], np.uint32); v = np.array([1, 2, 9], np.uint32); t = np.arange(3, dtype=np.int64)
         recs = run(srv, [(7, 6, u, v, t, np.array([0, 3], np.uint64))])
     assert recs[7]["status"] == tn.TN_ERANGE
+
+
+def test_batches_that_split_timestamp_groups():
+    """Batch boundaries inside timestamp groups (Section 2.1: a group is one
+    snapshot) are moved to the groups' ends, so every group is applied whole:
+    the out-sizes equal the one-shot call and the oracle.  One job has a single
+    giant group spanning several batches (its later batches become empty)."""
+    jobs = []
+    for jid, (n, m, t_range) in enumerate([(400, 6000, 60), (900, 12_000, 300), (300, 3000, 1)], start=50):
+        u, v, t = synth.uniform_events(n, m, t_range=t_range, seed=jid)
+        starts = np.flatnonzero(np.r_[True, t[1:] != t[:-1]])
+        inside = np.setdiff1d(np.arange(1, m), starts)  # cut positions between equal timestamps
+        cuts = np.sort(np.random.default_rng(jid).choice(inside, 5, replace=False))
+        offs = np.r_[0, cuts, m].astype(np.uint64)
+        jobs.append((jid, n, u, v, t, offs))
+    with tn.Server(max_active=4) as srv:
+        recs = run(srv, jobs)
+        results = dict(srv.results)
+    for jid, n, u, v, t, offs in jobs:
+        assert recs[jid]["status"] == 0, jid
+        assert np.array_equal(results[jid][0], tn.tn_out_component_sizes_host(u, v, t, n)[0]), jid
+        want = oracle.column_counts(oracle.component_matrix(u, v, t, n), n)
+        assert np.array_equal(results[jid][0], want), jid
