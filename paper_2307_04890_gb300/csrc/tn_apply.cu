@@ -255,7 +255,8 @@ __device__ inline void apply_tile(const Job &J, const uint2 *ops, uint32_t count
 
 // ---------------------------------------------------------------------------
 // local record: the window's rows are gathered into shared memory, its levels
-// are applied there, and the rows are written back
+// are applied there, and every written row goes back to the matrix from the op
+// that writes it for the last time (rows that are only read are not stored)
 // ---------------------------------------------------------------------------
 template <bool kMax>
 __device__ inline void apply_record(const Job &J, const uint32_t *rec, u64x2 *buf, const Lane &L)
@@ -294,7 +295,8 @@ __device__ inline void apply_record(const Job &J, const uint32_t *rec, u64x2 *bu
                     const uint32_t idx = o + k * stride;
                     live[k] = idx < e;
                     op[k] = live[k] ? ops[idx] : (kPull << kKindShift);
-                    const uint32_t kind = op[k] >> kKindShift, a = (op[k] >> 15) & kLocalMask, b = op[k] & kLocalMask;
+                    const uint32_t kind = op[k] >> kKindShift, a = (op[k] >> kLocalBits) & kLocalMask,
+                                   b = op[k] & kLocalMask;
                     if (kind != kPull) {
                         x[k] = lds16(mine + a * cpr);
                         y[k] = lds16(mine + b * cpr);
@@ -302,13 +304,19 @@ __device__ inline void apply_record(const Job &J, const uint32_t *rec, u64x2 *bu
                 }
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
-                    const uint32_t kind = op[k] >> kKindShift, a = (op[k] >> 15) & kLocalMask, b = op[k] & kLocalMask;
+                    const uint32_t kind = op[k] >> kKindShift, a = (op[k] >> kLocalBits) & kLocalMask,
+                                   b = op[k] & kLocalMask;
+                    // a row's last write in the window also goes to the matrix (write-through)
                     if (kind == kEvent) {
                         const u64x2 r = combine16<kMax>(x[k], y[k]);
                         sts16(mine + a * cpr, r);
                         sts16(mine + b * cpr, r);
+                        if (op[k] & kLastA) st_row16(J.S + (uint64_t)rows[a] * J.ld + col, r);
+                        if (op[k] & kLastB) st_row16(J.S + (uint64_t)rows[b] * J.ld + col, r);
                     } else if (kind == kOneway) {
-                        sts16(mine + a * cpr, combine16<kMax>(x[k], y[k]));
+                        const u64x2 r = combine16<kMax>(x[k], y[k]);
+                        sts16(mine + a * cpr, r);
+                        if (op[k] & kLastA) st_row16(J.S + (uint64_t)rows[a] * J.ld + col, r);
                     } else if (kind == kCopy) {
                         sts16(mine + a * cpr, y[k]);
                     } else if (live[k]) {
@@ -316,27 +324,14 @@ __device__ inline void apply_record(const Job &J, const uint32_t *rec, u64x2 *bu
                         const uint32_t c = aux[b];
                         for (uint32_t q = 1; q <= c; ++q) acc = combine16<kMax>(acc, lds16(mine + aux[b + q] * cpr));
                         sts16(mine + a * cpr, acc);
+                        if (op[k] & kLastA) st_row16(J.S + (uint64_t)rows[a] * J.ld + col, acc);
                     }
                 }
             }
         }
         consumers_sync();
     }
-    if (active) {
-        uint32_t d = lane0;
-        for (; d + 3 * stride < D; d += 4 * stride) {
-            u64x2 r[4];
-            uint32_t g[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                r[k] = lds16(mine + (d + k * stride) * cpr);
-                g[k] = rows[d + k * stride];
-            }
-#pragma unroll
-            for (int k = 0; k < 4; ++k) st_row16(J.S + (uint64_t)g[k] * J.ld + col, r[k]);
-        }
-        for (; d < D; d += stride) st_row16(J.S + (uint64_t)rows[d] * J.ld + col, lds16(mine + d * cpr));
-    }
+    // no write-back pass: every written row was stored at its last write
 }
 
 template <bool kMax>

@@ -52,19 +52,26 @@ __host__ __device__ inline uint32_t op_a(uint32_t kind, uint32_t id) { return (k
 //   local record (uint32 words): D, T, nlev, nops | rows[D] (node ids) |
 //     lvl[nlev + 1] (op offsets) | ops[nops] | aux[...] | zero padding to 16 B.
 //     Rows are named by local slots: 0..D-1 the window's rows, D..D+T-1 saved
-//     copies.  op = kind << 30 | a << 15 | b  (PULL: b = aux offset).
+//     copies.  op = kind << 30 | la << 29 | lb << 28 | a << 14 | b  (PULL: b =
+//     aux offset).  la / lb mark the op that writes row a / b for the last time
+//     in the window: its result is also stored to the matrix right away, so the
+//     write-back runs during the levels instead of after them, and rows that
+//     are only read are never written back.
 //   global tile: uint2 ops as above (node ids, absolute aux indices).
 // item = {offset in 8-byte units, count (global: ops; local: 8-byte units), flags, 0}
 constexpr uint32_t kStageBytes = 16384;
 constexpr uint32_t kTileOps = kStageBytes / 8 - 2;
 constexpr uint32_t kItemLocal = 1u;
 constexpr uint32_t kItemLevelEnd = 2u;
-constexpr uint32_t kLocalMask = 0x7FFFu;
-constexpr uint32_t kLocalSlotLimit = 0x7FFFu;
+constexpr uint32_t kLocalBits = 14;
+constexpr uint32_t kLocalMask = 0x3FFFu;
+constexpr uint32_t kLocalSlotLimit = 0x3FFFu;  // above the 10,240 slots a 160 KB row buffer can hold
+constexpr uint32_t kLastA = 1u << 29;
+constexpr uint32_t kLastB = 1u << 28;
 
 __host__ __device__ inline uint32_t local_op(uint32_t kind, uint32_t a, uint32_t b)
 {
-    return (kind << kKindShift) | (a << 15) | b;
+    return (kind << kKindShift) | (a << kLocalBits) | b;
 }
 
 __device__ inline void record_status(int32_t *status, int32_t code)

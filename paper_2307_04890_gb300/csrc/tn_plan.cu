@@ -508,6 +508,26 @@ __device__ void schedule_window(const PlanArgs &a, uint32_t w, uint32_t *arena)
             rops[atomicAdd(&lh[L], 1u)] = local_op(kPull, run_node[r], run_aux[r]);
             if (run_temp[r] != kNone) rops[atomicAdd(&lh[L - 1], 1u)] = local_op(kCopy, D + run_temp[r], run_node[r]);
         }
+        // last write of every row: ops are in level order and a level writes a
+        // row at most once, so it is the op with the highest index writing it
+        uint32_t *lastw = scratch + maxlev + 2;  // lh holds scratch[0 .. maxlev]
+        for (uint32_t d = tid; d < D; d += T) lastw[d] = 0;
+        __syncthreads();
+        for (uint32_t i = tid; i < nops; i += T) {
+            const uint32_t op = rops[i], kind = op >> kKindShift;
+            if (kind == kCopy) continue;  // writes a saved copy, not a row
+            atomicMax(&lastw[(op >> kLocalBits) & kLocalMask], i + 1);
+            if (kind == kEvent) atomicMax(&lastw[op & kLocalMask], i + 1);
+        }
+        __syncthreads();
+        for (uint32_t i = tid; i < nops; i += T) {
+            uint32_t op = rops[i];
+            const uint32_t kind = op >> kKindShift;
+            if (kind == kCopy) continue;
+            if (lastw[(op >> kLocalBits) & kLocalMask] == i + 1) op |= kLastA;
+            if (kind == kEvent && lastw[op & kLocalMask] == i + 1) op |= kLastB;
+            rops[i] = op;
+        }
         if (tid == 0) {
             cnt[0] = 0;
             cnt[1] = maxlev;

@@ -255,3 +255,39 @@ def test_online_equals_one_shot_at_scale():
     got = ((ref[:, torch.from_numpy(cols.astype(np.int64) // 64).cuda()]
             >> torch.from_numpy(cols.astype(np.int64) % 64).cuda()) & 1).bool().cpu().numpy()
     assert np.array_equal(got, want)
+
+
+def test_hashed_network_streamed_with_new_nodes():
+    """Section 4 with Section 3.5: the hash is a function of the node id, so the
+    tables of a grown network extend those of the smaller one, and the k x k
+    proxy matrices never grow.  Streaming the super-events of batches whose
+    later part names new nodes through R online states (groups split across
+    batches) gives the same proxies and estimates as the one-shot hashed path
+    over the final network, and the oracle's."""
+    n0, n1, k, R, seed = 1500, 2600, 256, 4, 9
+    rng = np.random.default_rng(seed)
+    m0, m1 = 20_000, 30_000
+    u = np.r_[rng.integers(0, n0, m0), rng.integers(0, n1, m1)].astype(np.uint32)
+    v = np.r_[rng.integers(0, n0, m0), rng.integers(0, n1, m1)].astype(np.uint32)
+    t = np.r_[np.sort(rng.integers(0, 500, m0)), np.sort(rng.integers(499, 1000, m1))].astype(np.int64)
+    du, dv, dt = dev(u), dev(v), dev(t, np.int64)
+    H0, _, _ = tn.tn_hash_proxy(None, None, n0, k, R, seed, events=False)
+    H1, pu, pv = tn.tn_hash_proxy(du, dv, n1, k, R, seed)
+    assert torch.equal(H1[:, :n0], H0)  # the grown network's tables extend the old ones
+    states = [tn.Online(k) for _ in range(R)]
+    for a, b in cuts_through_groups(t, rng, 10):
+        for j in range(R):
+            states[j].push(pu[j, a:b].contiguous(), pv[j, a:b].contiguous(), dt[a:b])
+    P_stream = torch.empty((R, k, tn.tn_row_words(k)), dtype=torch.int64, device="cuda")
+    for j in range(R):
+        states[j].flush()
+        P_stream[j].copy_(states[j].matrix())
+        states[j].close()
+    P_batch = torch.empty_like(P_stream)
+    plans = [tn.Plan(pu[j].contiguous(), pv[j].contiguous(), dt, k) for j in range(R)]
+    tn.tn_plan_apply_batch(plans, [P_batch[j] for j in range(R)])
+    assert torch.equal(P_stream, P_batch)
+    est = tn.tn_hash_estimate(P_stream, R, k, H1, n1).cpu().numpy().view(np.uint32)
+    Href = oracle.hash_nodes(seed, R, k, n1)
+    want = oracle.hash_estimate(oracle.proxy_matrices(u, v, t, Href, k), Href, n1)
+    assert np.array_equal(est, want)
