@@ -31,9 +31,15 @@ sys.path.insert(0, ROOT)
 
 METRIC = "events/s and bit-updates/s (n·m/time) at 1 GB300; achieved HBM GB/s vs peak"
 ONLINE_METRIC = "events/s through the online state (batches that split timestamp groups)"
-PROFILE_SUMMARIES = {"activity": "stream_kernel_activity_n1e5_m1e7.txt",
-                     "bursty": "stream_kernel_bursty_n5e5_m1e8.txt"}
-KERNEL_SOURCES = ["paper_2307_04890_gb300/csrc/tn_apply.cu", "paper_2307_04890_gb300/csrc/tn_internal.cuh"]
+# ncu summaries under profiles/ and the sources whose hash they record (a summary
+# taken on other sources gives no traffic figure)
+STREAM_SOURCES = ["paper_2307_04890_gb300/csrc/tn_apply.cu", "paper_2307_04890_gb300/csrc/tn_internal.cuh",
+                  "paper_2307_04890_gb300/csrc/tn_plan.cu"]
+PROFILE_SUMMARIES = {"activity": ("stream_kernel_activity_n1e5_m1e7.txt", STREAM_SOURCES),
+                     "bursty": ("stream_kernel_bursty_n5e5_m1e8.txt", STREAM_SOURCES),
+                     "online": ("grow_kernel_online_n1e5_to_102048.txt",
+                                ["paper_2307_04890_gb300/csrc/tn_online.cu",
+                                 "paper_2307_04890_gb300/csrc/tn_internal.cuh"])}
 
 WORKLOADS = {
     "activity": dict(desc="activity-driven n=100000 m=10000000 (power-law activity 2.1, a_min 1e-3, us ticks)",
@@ -110,25 +116,26 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def kernel_source_sha():
+def kernel_source_sha(sources):
     h = hashlib.sha256()
-    for rel in KERNEL_SOURCES:
+    for rel in sources:
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
 def profiled_traffic(workload_key):
-    """DRAM bytes per launch of the stream kernel from the committed ncu summary,
-    if it was taken on the current kernel source and this workload."""
+    """DRAM bytes per launch of the workload's dominant kernel from the committed
+    ncu summary, if it was taken on the current kernel sources and this workload."""
     try:
         fields = {}
-        with open(os.path.join(ROOT, "profiles", PROFILE_SUMMARIES[workload_key])) as f:
+        name, sources = PROFILE_SUMMARIES[workload_key]
+        with open(os.path.join(ROOT, "profiles", name)) as f:
             for line in f:
                 if ":" in line and not line.startswith("#"):
                     k, v = line.split(":", 1)
                     fields[k.strip()] = v.strip()
-        if fields.get("kernel_source_sha256_16") != kernel_source_sha():
+        if fields.get("kernel_source_sha256_16") != kernel_source_sha(sources):
             return None
         if fields.get("workload") != workload_key:
             return None
@@ -633,7 +640,8 @@ def run_online(args, w, rank, world, local_rank):
               "roofline": {"bound": "hbm", "kernel": "grow_kernel (growth %d -> %d nodes into a new buffer)" % (n, n2),
                            "achieved": grow_bytes / (grow_ms * 1e-3) / 1e9, "peak": peak,
                            "peak_source": f"{peak_kind} MEASURED_PEAKS hbm_gbs", "unit": "GB/s",
-                           "frac": grow_bytes / (grow_ms * 1e-3) / 1e9 / peak, "traffic": None,
+                           "frac": grow_bytes / (grow_ms * 1e-3) / 1e9 / peak,
+                           "traffic": profiled_traffic("online"),
                            "algorithmic_bytes_per_launch": grow_bytes, "kernel_ms": grow_ms, "correct": grown_ok},
               "gpu_launches": launches, "clocks": clocks.summary()}
     if rank == 0:
