@@ -4,10 +4,12 @@
 //
 // One CTA covers 1024 consecutive columns (32 lanes x one 32-bit word each)
 // and a block of rows; its 8 warps take interleaved rows.  Column counts are
-// accumulated in bit-sliced vertical counters: four registers hold bits 0..3
-// of 32 per-column counts, so adding a row word costs a short carry chain
-// instead of 32 extractions; every 15 rows the counters are flushed into
-// per-thread integer counts.  Row counts come from __popc and a warp sum.
+// accumulated in bit-sliced vertical counters: eight registers hold bits 0..7
+// of 32 per-column counts, so adding a row word costs a carry chain instead of
+// 32 extractions; every 255 rows the counters are flushed into the thread's
+// 32 integer counts in shared memory (registers stay free for loads in flight).  Row counts come from __popc and a warp sum.
+// Each warp loads kRowBatch rows before folding any of them in, so that
+// enough loads are in flight per SM to keep HBM busy.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -17,8 +19,10 @@ namespace tn {
 
 constexpr int kSizeWarps = 8;
 constexpr uint32_t kRowsPerBlock = 2048;
+constexpr int kRowBatch = 16;
+constexpr int kCounterBits = 8;  // vertical counters hold up to 2^8 - 1
 
-__global__ void __launch_bounds__(32 * kSizeWarps)
+__global__ void __launch_bounds__(32 * kSizeWarps, 4)
     column_counts_kernel(const uint32_t *S32, uint32_t n_rows, uint64_t ld32, uint32_t ncols, uint32_t *out,
                          uint32_t *in)
 {
@@ -29,39 +33,55 @@ __global__ void __launch_bounds__(32 * kSizeWarps)
     const uint32_t r0 = blockIdx.y * kRowsPerBlock;
     const uint32_t r1 = min(n_rows, r0 + kRowsPerBlock);
 
-    uint32_t cnt[32];
+    uint32_t *cnt = part[warp][lane];  // this thread's 32 column counts
 #pragma unroll
     for (int b = 0; b < 32; ++b) cnt[b] = 0;
-    uint32_t c0 = 0, c1 = 0, c2 = 0, c3 = 0, pending = 0;
-    for (uint32_t r = r0 + warp; r < r1; r += kSizeWarps) {
-        const uint32_t x = live ? __ldcs(S32 + (uint64_t)r * ld32 + word) : 0u;
-        if (in) {
-            uint32_t pc = __popc(x);
+    uint32_t vc[kCounterBits];
 #pragma unroll
-            for (int d = 16; d > 0; d >>= 1) pc += __shfl_xor_sync(0xffffffffu, pc, d);
-            if (lane == 0 && pc) atomicAdd(&in[r], pc);
-        }
-        // add x to the 4-bit vertical counters
-        uint32_t carry = c0 & x;
-        c0 ^= x;
-        uint32_t carry2 = c1 & carry;
-        c1 ^= carry;
-        uint32_t carry3 = c2 & carry2;
-        c2 ^= carry2;
-        c3 ^= carry3;
-        if (++pending == 15) {
+    for (int j = 0; j < kCounterBits; ++j) vc[j] = 0;
+    uint32_t pending = 0;
+    // adds the vertical counters into the integer counts and clears them
+    auto flush = [&]() {
+#pragma unroll 4
+        for (int b = 0; b < 32; ++b) {
+            uint32_t v = 0;
 #pragma unroll
-            for (int b = 0; b < 32; ++b)
-                cnt[b] += ((c0 >> b) & 1u) + (((c1 >> b) & 1u) << 1) + (((c2 >> b) & 1u) << 2) + (((c3 >> b) & 1u) << 3);
-            c0 = c1 = c2 = c3 = 0;
-            pending = 0;
+            for (int j = 0; j < kCounterBits; ++j) v |= ((vc[j] >> b) & 1u) << j;
+            cnt[b] += v;
         }
+#pragma unroll
+        for (int j = 0; j < kCounterBits; ++j) vc[j] = 0;
+        pending = 0;
+    };
+    for (uint32_t rb = r0 + warp; rb < r1; rb += kRowBatch * kSizeWarps) {
+        uint32_t xs[kRowBatch];
+#pragma unroll
+        for (int k = 0; k < kRowBatch; ++k) {
+            const uint32_t r = rb + k * kSizeWarps;
+            xs[k] = (live && r < r1) ? __ldcs(S32 + (uint64_t)r * ld32 + word) : 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < kRowBatch; ++k) {
+            const uint32_t r = rb + k * kSizeWarps;
+            if (in && r < r1) {
+                uint32_t pc = __popc(xs[k]);
+#pragma unroll
+                for (int d = 16; d > 0; d >>= 1) pc += __shfl_xor_sync(0xffffffffu, pc, d);
+                if (lane == 0 && pc) atomicAdd(&in[r], pc);
+            }
+            // add the row word to the vertical counters (rows past the block add 0)
+            uint32_t carry = xs[k];
+#pragma unroll
+            for (int j = 0; j < kCounterBits; ++j) {
+                const uint32_t next = vc[j] & carry;
+                vc[j] ^= carry;
+                carry = next;
+            }
+        }
+        pending += kRowBatch;
+        if (pending + kRowBatch > (1u << kCounterBits) - 1u) flush();
     }
-#pragma unroll
-    for (int b = 0; b < 32; ++b)
-        cnt[b] += ((c0 >> b) & 1u) + (((c1 >> b) & 1u) << 1) + (((c2 >> b) & 1u) << 2) + (((c3 >> b) & 1u) << 3);
-#pragma unroll
-    for (int b = 0; b < 32; ++b) part[warp][lane][b] = cnt[b];
+    flush();
     __syncthreads();
     // thread t sums column (t / 32, bit t % 32) of this block over the warps
     for (uint32_t c = threadIdx.x; c < 1024; c += blockDim.x) {
