@@ -628,23 +628,37 @@ __global__ void window_scan_kernel(const uint32_t *wcount, uint32_t nw, uint64_t
         levels = ops = local = 0;
     }
     __syncthreads();
-    const int field[3] = {6, 5, 2};
+    static_assert(kWinFields == 8, "two 16-byte loads per window");
     for (uint32_t c0 = 0; c0 < nw; c0 += blockDim.x) {
         const uint32_t w = c0 + threadIdx.x;
-        const uint32_t *c = wcount + (uint64_t)kWinFields * w;
+        uint4 lo = make_uint4(0u, 0u, 0u, 0u), hi = make_uint4(0u, 0u, 0u, 0u);
+        if (w < nw) {
+            const uint4 *c = reinterpret_cast<const uint4 *>(wcount + (uint64_t)kWinFields * w);
+            lo = c[0];  // nops, nlev, naux, ntemp
+            hi = c[1];  // local, blob8, nitems, all ops
+        }
+        const uint32_t x[3] = {hi.z, hi.y, lo.z};  // items, blob8, naux
         for (int k = 0; k < 3; ++k) {
-            uint32_t x = w < nw ? c[field[k]] : 0u;
-            uint32_t ex = block_excl_scan_value(x, warp_sums, &total);
+            uint32_t ex = block_excl_scan_value(x[k], warp_sums, &total);
             if (w < nw) base[3ull * w + k] = carry[k] + ex;
             __syncthreads();
             if (threadIdx.x == 0) carry[k] += total;
             __syncthreads();
         }
-        if (w < nw) {
-            atomicMax(&tmax, c[3]);
-            atomicAdd(&levels, (unsigned long long)c[1]);
-            atomicAdd(&ops, (unsigned long long)c[7]);
-            atomicAdd(&local, (unsigned long long)c[4]);
+        // totals: a warp reduction first, then one shared atomic per warp
+        unsigned long long lv = lo.y, op = hi.w, lc = hi.x;
+        uint32_t tm = lo.w;
+        for (int d = 16; d > 0; d >>= 1) {
+            lv += __shfl_xor_sync(0xffffffffu, lv, d);
+            op += __shfl_xor_sync(0xffffffffu, op, d);
+            lc += __shfl_xor_sync(0xffffffffu, lc, d);
+            tm = max(tm, __shfl_xor_sync(0xffffffffu, tm, d));
+        }
+        if ((threadIdx.x & 31u) == 0) {
+            atomicMax(&tmax, tm);
+            atomicAdd(&levels, lv);
+            atomicAdd(&ops, op);
+            atomicAdd(&local, lc);
         }
     }
     __syncthreads();
@@ -697,10 +711,12 @@ __global__ void compact_kernel(PlanArgs a, const uint64_t *base, uint2 *blob, ui
     }
 }
 
-__global__ void tbounds_kernel(const int64_t *t, uint64_t m, int64_t *out)
+// the batch's time bounds, known on the host, into the plan (no read of t, so
+// the caller may free the events as soon as tn_plan_create returns)
+__global__ void tbounds_kernel(int64_t t_first, int64_t t_last, int64_t *out)
 {
-    out[0] = t[0];
-    out[1] = t[m - 1];
+    out[0] = t_first;
+    out[1] = t_last;
 }
 
 // shared-memory budget of the per-window scheduler
@@ -808,6 +824,9 @@ extern "C" tn_status tn_plan_create(const uint32_t *u, const uint32_t *v, const 
     big_window_kernel<<<wblocks, 256, 0, st>>>(a);
     TN_STEP(cudaGetLastError());
     TN_STEP(cudaMemcpyAsync(host_counters, a.counters, sizeof(host_counters), cudaMemcpyDeviceToHost, st));
+    // the batch's time bounds travel with the first synchronisation
+    TN_STEP(cudaMemcpyAsync(&p->t_first, t, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    TN_STEP(cudaMemcpyAsync(&p->t_last, t + (m - 1), sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     TN_STEP(cudaStreamSynchronize(st));
     if (host_counters[0] & 1ull) {
         rc = TN_ERANGE;
@@ -858,16 +877,10 @@ extern "C" tn_status tn_plan_create(const uint32_t *u, const uint32_t *v, const 
     TN_STEP(cudaMemsetAsync(p->d_status, 0, sizeof(int32_t), st));
     tn_internal_count_launches(2);
     compact_kernel<<<a.nw, 256, 0, st>>>(a, base, p->d_blob, p->d_items, p->d_aux);
-    tbounds_kernel<<<1, 1, 0, st>>>(t, m, p->d_tbounds);
+    tbounds_kernel<<<1, 1, 0, st>>>(p->t_first, p->t_last, p->d_tbounds);
     TN_STEP(cudaGetLastError());
-    {
-        int64_t tb[2];
-        TN_STEP(cudaMemcpyAsync(tb, t, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-        TN_STEP(cudaMemcpyAsync(tb + 1, t + (m - 1), sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-        TN_STEP(cudaStreamSynchronize(st));
-        p->t_first = tb[0];
-        p->t_last = tb[1];
-    }
+    // the plan is complete when this call returns, for use on any stream
+    TN_STEP(cudaStreamSynchronize(st));
     goto done;
 
 fail:
