@@ -24,9 +24,12 @@
 
 namespace tn {
 
-constexpr int kConsumerWarps = 4;
-constexpr int kConsumers = 32 * kConsumerWarps;
-constexpr int kThreads = kConsumers + 32;
+// Consumer warps per CTA, chosen at launch: 12 when a CTA's row buffer leaves
+// no room for a second CTA on the SM, 4 when two CTAs share an SM (both then
+// fit in the register file).  The producer is one more warp.
+constexpr int kWarpsAlone = 12;
+constexpr int kWarpsShared = 4;
+constexpr int kMaxThreads = 32 * kWarpsAlone + 32;
 constexpr int kStages = 2;
 constexpr uint32_t kEndItem = 0xFFFFFFFFu;
 constexpr int kMaxJobs = 24;
@@ -73,13 +76,16 @@ struct Lane {
     bool active;   // chunk inside the matrix and thread inside the row groups
 };
 
+// consumer threads of this launch (all warps but the producer)
+__device__ inline uint32_t consumers() { return blockDim.x - 32u; }
+
 __device__ inline Lane make_lane(const Job &J, uint32_t ct, uint64_t w0)
 {
     Lane L;
     L.cpr = J.cpr;
     L.chunk = ct % L.cpr;
     L.lane0 = ct / L.cpr;
-    L.stride = (uint32_t)kConsumers / L.cpr;
+    L.stride = consumers() / L.cpr;
     L.col = w0 + 2ull * L.chunk;
     L.active = L.lane0 < L.stride && L.col < J.ld;
     return L;
@@ -91,7 +97,7 @@ __device__ inline uint64_t *row_ptr(const Job &J, uint32_t ref, uint64_t col)
     return J.S + (uint64_t)ref * J.ld + col;
 }
 
-__device__ inline void consumers_sync() { asm volatile("bar.sync 1, %0;" ::"r"(kConsumers) : "memory"); }
+__device__ inline void consumers_sync() { asm volatile("bar.sync 1, %0;" ::"r"(consumers()) : "memory"); }
 
 // Barrier of the consumer warps (named barrier 1) that also ORs a predicate
 // across them, so that every consumer takes the same decision to stop.
@@ -104,7 +110,7 @@ __device__ inline bool consumers_sync_or(bool p)
         "bar.red.or.pred op, 1, %2, ip;\n\t"
         "selp.u32 %0, 1, 0, op;\n\t}"
         : "=r"(r)
-        : "r"((uint32_t)p), "r"(kConsumers)
+        : "r"((uint32_t)p), "r"(consumers())
         : "memory");
     return r != 0;
 }
@@ -335,7 +341,7 @@ __device__ inline void apply_record(const Job &J, const uint32_t *rec, u64x2 *bu
 }
 
 template <bool kMax>
-__global__ void __launch_bounds__(kThreads) stream_kernel(const __grid_constant__ JobList jl)
+__global__ void __launch_bounds__(kMaxThreads) stream_kernel(const __grid_constant__ JobList jl)
 {
     extern __shared__ __align__(128) uint8_t smem[];
     uint8_t *stage = smem;  // kStages x kStageBytes
@@ -353,7 +359,7 @@ __global__ void __launch_bounds__(kThreads) stream_kernel(const __grid_constant_
         gate = *(volatile int32_t *)J.status;  // an earlier error gates this job
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], kConsumerWarps);
+            mbar_init(&empty[s], consumers() / 32u);
         }
         producer_abort = 0;
         fence_mbar_init();
@@ -595,13 +601,17 @@ tn_status apply_jobs(const tn_plan *const *plans, uint64_t *const *S, const uint
         TN_CUDA_TRY(cudaGetLastError());
         if (ctas) {
             tn_internal_count_launches(1);
-            if (flags & kApplyMax) {
-                TN_CUDA_TRY(tn_internal_allow_max_dyn_smem((const void *)stream_kernel<true>));
-                stream_kernel<true><<<ctas, kThreads, smem, st>>>(jl);
-            } else {
-                TN_CUDA_TRY(tn_internal_allow_max_dyn_smem((const void *)stream_kernel<false>));
-                stream_kernel<false><<<ctas, kThreads, smem, st>>>(jl);
-            }
+            const void *kernel = (flags & kApplyMax) ? (const void *)stream_kernel<true> : (const void *)stream_kernel<false>;
+            TN_CUDA_TRY(tn_internal_allow_max_dyn_smem(kernel));
+            // 4 consumer warps if two CTAs of that size fit on an SM, else 12
+            int pair = 0;
+            const int shared_threads = 32 * kWarpsShared + 32;
+            TN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pair, kernel, shared_threads, smem));
+            const int threads = pair >= 2 ? shared_threads : kMaxThreads;
+            if (flags & kApplyMax)
+                stream_kernel<true><<<ctas, threads, smem, st>>>(jl);
+            else
+                stream_kernel<false><<<ctas, threads, smem, st>>>(jl);
         }
         TN_CUDA_TRY(cudaGetLastError());
         for (uint32_t j = 0; j < nj; ++j) {
