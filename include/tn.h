@@ -189,7 +189,10 @@ typedef struct tn_plan_options {
     uint32_t smem_rows;     /* row slots of the streaming kernel's shared-memory row
                                buffer (at most 160 KB / (8 slab_words)); windows with
                                more rows (plus saved copies) stream from global
-                               memory (0 = 160 KB / (8 slab_words)) */
+                               memory (0 = 160 KB / (8 slab_words)).  A buffer small
+                               enough for two CTAs per SM (about 80 KB) runs two CTAs
+                               of 4 consumer warps per SM; a larger one runs one CTA
+                               of 12 consumer warps */
     uint32_t directed;      /* 1: event (u, v, t) is directed u -> v and only S[v] is
                                updated, S[v] |= S[u] (the paper's footnote to Section
                                3.1); timestamp groups stay snapshots.  0: undirected */
