@@ -466,7 +466,7 @@ tn_status tn_server_destroy(tn_server *server);
 /* ---------------------------------------------------------------------------
  * Node growth (Section 3.5, advantages and limitations of the matrix method:
  * a node that joins the network adds a row and a column to the component
- * matrix, "False" except the diagonal element).
+ * matrix: zeros, except the new node's own diagonal bit).
  *
  * tn_grow_matrix -- S_new (n_new x n_new, layout above) receives S_old
  * (n_old x n_old) in its first n_old rows and columns, with bits of columns

@@ -14,8 +14,9 @@ arrays.  Functions cite the paper passage they follow:
   (footnote to Section 3.1: only the receiver's row is updated).
 * ``hll_singleton`` / ``hll_sketches`` / ``hll_estimate`` -- HyperLogLog
   sketches of the components and their size estimates (Section 3.4).
-* ``grow_matrix``       -- node growth: a new row and column, False except the
-  diagonal (Section 3.5, advantages and limitations of the matrix method).
+* ``grow_matrix``       -- node growth: a new row and column of zeros with the
+  new node's diagonal bit set (Section 3.5, advantages and limitations of the
+  matrix method).
 * ``si_reach``          -- the deterministic SI process (Section 1).
 * ``column_counts`` / ``row_counts`` / ``argmax`` -- component sizes
   (Section 3.1, eq. for the mean size s_t in Section 3.3).
@@ -210,8 +211,8 @@ def si_reach(u, v, t, n, source) -> np.ndarray:
 
 def grow_matrix(S: np.ndarray, n_old: int, n_new: int) -> np.ndarray:
     """Node growth (Section 3.5): the n_old x n_old matrix S extended to n_new
-    nodes, each new node a new row and column that is False except on the
-    diagonal.  Returns a new n_new x words(n_new) matrix."""
+    nodes, each new node a new row and column of zeros with its own diagonal
+    bit set.  Returns a new n_new x words(n_new) matrix."""
     S = np.ascontiguousarray(S, dtype=np.uint64)
     assert S.shape[0] == n_old
     out = np.zeros((n_new, max(1, words(n_new))), dtype=np.uint64)

@@ -311,8 +311,8 @@ int tnref_si_reach(const uint32_t *u, const uint32_t *v, const int64_t *t,
 
 /* ---------------------------------------------------------------------------
  * Node growth (Section 3.5, advantages and limitations of the matrix method):
- * a node that joins the network adds one row and one column, all "False"
- * except the diagonal element.  S_old is n_old x n_old (row stride w_old
+ * a node that joins the network brings a new row and a new column of zeros,
+ * with only its own diagonal bit set.  S_old is n_old x n_old (row stride w_old
  * words), S_new is n_new x n_new (row stride w_new words), n_new >= n_old:
  *   S_new[i][j] = S_old[i][j]  for i, j < n_old,
  *   S_new[i][i] = 1            for n_old <= i < n_new,

@@ -575,7 +575,7 @@ def tn_hll_estimate(R, n: int, p: int, stream=None):
 
 def tn_grow_matrix(S, n_old: int, n_new: int, out=None, stream=None):
     """Node growth (Section 3.5): S (n_old x n_old) extended by new rows and
-    columns that are False except the diagonal.  Writes into ``out`` (a new
+    columns of zeros with only the new nodes' diagonal bits set.  Writes into ``out`` (a new
     n_new x tn_row_words(n_new) tensor when None; ``out is S`` grows in place,
     which needs an unchanged row stride and room for n_new rows)."""
     lib = load_library()

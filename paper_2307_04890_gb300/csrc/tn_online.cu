@@ -2,8 +2,8 @@
 // method): a component matrix that stays on the device while event batches and
 // new nodes arrive.
 //
-//  * Node growth: a new node adds a row and a column that are "False" except on
-//    the diagonal.  grow_kernel rewrites a matrix in the padded row layout for
+//  * Node growth: a new node brings a row and a column of zeros with only its
+//    own diagonal bit set.  grow_kernel rewrites a matrix in the padded row layout for
 //    more nodes; when the row stride is unchanged it only touches the new rows
 //    and the new columns of the old rows.
 //  * Timestamp groups split across batches: a group is one snapshot (every

@@ -4,7 +4,7 @@ Section 3.5: the matrix method takes new events and new nodes as they arrive.
 Batches may split a timestamp group anywhere; after every push the matrix must
 equal the oracle over the events before the held-back last group, and after a
 flush the oracle over all of them.  Growth must equal the oracle's definition
-(new row and column, False except the diagonal).
+(new rows and columns of zeros with the new diagonal bits set).
 """
 import numpy as np
 import pytest

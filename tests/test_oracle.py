@@ -177,8 +177,8 @@ def test_incremental_equals_one_shot_and_monotone():
 
 
 # --------------------------------------------------------------------------
-# node growth (Section 3.5: a new node is a new row and column, False except
-# on the diagonal)
+# node growth (Section 3.5: a new node is a new row and column of zeros with
+# its own diagonal bit set)
 # --------------------------------------------------------------------------
 def _pack(B):
     B = np.asarray(B, dtype=bool)
