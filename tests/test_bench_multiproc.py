@@ -62,3 +62,16 @@ def test_reference_arm_prints_once_under_torchrun():
     rec = json.loads(lines[0])
     assert rec["impl"] == "reference" and rec["n_gpus"] == 2 and rec["value"] > 0
     assert rec["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_reference_arm_of_the_online_workload():
+    """The online workload's reference arm times the oracle on a prefix and
+    reports events/s, the unit of the online line."""
+    cmd = [sys.executable, "bench.py", "--impl", "reference", "--workload", "online", "--steps", "1",
+           "--warmup", "0", "--cpu-seconds", "0.5"]
+    res = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert res.returncode == 0, res.stderr[-2000:]
+    rec = json.loads([ln for ln in res.stdout.splitlines() if ln.startswith("{")][-1])
+    assert rec["impl"] == "reference" and rec["unit"] == "events/s" and rec["value"] > 0
+    assert rec["metric"].startswith("events/s through the online state")
+    assert rec["cpu_baseline"]["kind"] == "oracle" and rec["e2e"]["unit"] == "events/s"

@@ -67,3 +67,28 @@ def test_server_needs_a_device():
     with pytest.raises(tn.TnError) as exc:
         tn.Server()
     assert exc.value.status == tn.TN_ECUDA
+
+
+def test_growth_and_online_reject_bad_arguments_before_any_device_call(lib_path):
+    """Host-side argument checks of the node-growth and online-state entry
+    points return TN_EINVAL before touching a device (no GPU needed)."""
+    lib = tn.load_library()
+    vp = ctypes.c_void_p
+    fake = vp(0x1000)  # never dereferenced: every call below fails its argument checks first
+    assert lib.tn_grow_matrix(fake, 100, fake, 50, None) == tn.TN_EINVAL      # shrinking
+    assert lib.tn_grow_matrix(None, 10, fake, 20, None) == tn.TN_EINVAL       # no old matrix
+    assert lib.tn_grow_matrix(fake, 0, None, 20, None) == tn.TN_EINVAL        # no new matrix
+    assert lib.tn_grow_matrix(fake, 10, fake, 1 << 30, None) == tn.TN_EINVAL  # too many nodes
+    # in place is only allowed while the row stride stays (1000 -> 2000 nodes changes it)
+    assert lib.tn_grow_matrix(fake, 1000, fake, 2000, None) == tn.TN_EINVAL
+    # partially overlapping buffers
+    assert lib.tn_grow_matrix(vp(0x100000), 1000, vp(0x100000 + 4096), 1000, None) == tn.TN_EINVAL
+    h = vp()
+    assert lib.tn_online_create(0, None, None, ctypes.byref(h)) == tn.TN_EINVAL
+    assert lib.tn_online_create(1 << 30, None, None, ctypes.byref(h)) == tn.TN_EINVAL
+    assert lib.tn_online_create(10, None, None, None) == tn.TN_EINVAL
+    assert lib.tn_online_push(None, fake, fake, fake, 5, 0, None) == tn.TN_EINVAL
+    assert lib.tn_online_flush(None, None) == tn.TN_EINVAL
+    assert lib.tn_online_grow(None, 10, None) == tn.TN_EINVAL
+    assert lib.tn_online_status(None, None) == tn.TN_EINVAL
+    assert lib.tn_online_destroy(None, None) == tn.TN_EINVAL
