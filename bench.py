@@ -153,7 +153,8 @@ class ClockSampler:
 
     def __init__(self, gpu_index):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        import tempfile
+        self.path = os.path.join(tempfile.gettempdir(), f"tn_bench_clocks_{os.getpid()}.csv")
         self.gpu = gpu_index
 
     def __enter__(self):
