@@ -560,7 +560,8 @@ tn_status tn_online_get_state(const tn_online *online, tn_online_state *state);
 tn_status tn_online_destroy(tn_online *online, void *stream);
 
 /* ---------------------------------------------------------------------------
- * HyperLogLog sketches of the components (Section 3.4).  Approximate: O(n s)
+ * HyperLogLog sketches of the components (Section 3.3; with TN_REVERSE,
+ * Section 3.4).  Approximate: O(n s)
  * memory instead of n^2 bits, for the average component size (in-components,
  * Eq. s_t) or, with TN_REVERSE, the out-component size distribution.
  *

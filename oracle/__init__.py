@@ -13,7 +13,8 @@ arrays.  Functions cite the paper passage they follow:
 * ``component_matrix_directed`` / ``si_reach_directed`` -- directed events
   (footnote to Section 3.1: only the receiver's row is updated).
 * ``hll_singleton`` / ``hll_sketches`` / ``hll_estimate`` -- HyperLogLog
-  sketches of the components and their size estimates (Section 3.4).
+  sketches of the components and their size estimates (Section 3.3; with
+  the reversed sequence, Section 3.4).
 * ``grow_matrix``       -- node growth: a new row and column of zeros with the
   new node's diagonal bit set (Section 3.5, advantages and limitations of the
   matrix method).
@@ -332,7 +333,7 @@ def error_stats(est, exact) -> dict:
 
 
 def hll_singleton(seed: int, p: int, x: int):
-    """(register, rank) of element x in a sketch of 2^p registers (Section 3.4)."""
+    """(register, rank) of element x in a sketch of 2^p registers (Section 3.3)."""
     reg, rank = ctypes.c_uint32(), ctypes.c_uint8()
     _load().tnref_hll_singleton(seed, p, x, ctypes.byref(reg), ctypes.byref(rank))
     return reg.value, rank.value
@@ -340,7 +341,7 @@ def hll_singleton(seed: int, p: int, x: int):
 
 def hll_sketches(u, v, t, n: int, p: int, seed: int, reverse: bool = False, directed: bool = False) -> np.ndarray:
     """uint8[n, 2^p]: node i's sketch of its in-component (out-component with
-    reverse=True), merged by register-wise maximum per event (Section 3.4)."""
+    reverse=True), merged by register-wise maximum per event (Sections 3.3, 3.4)."""
     u, v, t = _ev(u, v, t)
     R = np.zeros((n, 1 << p), dtype=np.uint8)
     _check(_load().tnref_hll_sketches(u, v, t, len(u), n, p, seed, int(reverse), int(directed), R.reshape(-1)))

@@ -580,7 +580,8 @@ int tnref_si_reach_directed(const uint32_t *u, const uint32_t *v, const int64_t 
 }
 
 /* ---------------------------------------------------------------------------
- * HyperLogLog sketches of the components (Section 3.4; Flajolet, Fusy,
+ * HyperLogLog sketches of the components (Section 3.3, and Section 3.4 with
+ * the reversed sequence; Flajolet, Fusy,
  * Gandouet, Meunier 2007).  Each node keeps s = 2^p one-byte registers.  An
  * element x hashes to h = one SplitMix64 step from state (seed XOR x); its
  * register is the top p bits of h and its rank the position of the first 1 in

@@ -549,7 +549,7 @@ def tn_selftest_wait_timeout(stream=None) -> int:
 
 
 def tn_hll_sketches(u, v, t, n: int, p: int, seed: int, reverse: bool = False, directed: bool = False, stream=None):
-    """HyperLogLog sketches of the components (Section 3.4): uint8 [n, row_bytes];
+    """HyperLogLog sketches of the components (Section 3.3; reversed, Section 3.4): uint8 [n, row_bytes];
     the first 2^p bytes of row i are node i's registers."""
     torch = _torch()
     lib = load_library()

@@ -1,4 +1,5 @@
-// HyperLogLog sketches of the components (Section 3.4; Flajolet, Fusy,
+// HyperLogLog sketches of the components (Section 3.3, and Section 3.4 with the
+// reversed sequence; Flajolet, Fusy,
 // Gandouet, Meunier 2007).
 //
 // Node i keeps s = 2^p one-byte registers instead of a row of n bits.  Element

@@ -1,4 +1,4 @@
-"""HyperLogLog sketches of the components on the GPU (Section 3.4; needs a GPU: -m gpu).
+"""HyperLogLog sketches of the components on the GPU (Sections 3.3, 3.4; needs a GPU: -m gpu).
 
 Registers are integers: bit-exact to the oracle in every mode.  Estimates are
 doubles summed in another order: within 1e-12 relative.  Against the exact

@@ -577,7 +577,7 @@ def test_directed_exhaustive_tiny():
 
 
 # --------------------------------------------------------------------------
-# HyperLogLog sketches of the components (Section 3.4)
+# HyperLogLog sketches of the components (Section 3.3; reversed, Section 3.4)
 # --------------------------------------------------------------------------
 def _singletons(seed, p, n):
     s = 1 << p
