@@ -21,8 +21,11 @@ arrays.  Functions cite the paper passage they follow:
 * ``si_reach``          -- the deterministic SI process (Section 1).
 * ``column_counts`` / ``row_counts`` / ``argmax`` -- component sizes
   (Section 3.1, eq. for the mean size s_t in Section 3.3).
-* ``hash_*``            -- network hashing (Section 4.1; reading of the garbled
-  construction documented in tnref.c).  Exact constants: parity unpinned.
+* ``splitmix64_stream`` / ``hash_*`` -- network hashing (Section 4.1; reading
+  of the garbled construction documented in tnref.c).  The generator is
+  pinned by its known-answer values, the coefficients and tables by big-integer
+  restatements; agreement with the authors' own unpublished hash values cannot
+  be checked.
 * ``hash_estimate``     -- fusion by intersection (Section 4.2, eqs.
   DefInvHComp, DefEstOCMerge).
 * ``emd_w1``            -- Earth-Mover (Wasserstein-1) distance between two
@@ -103,6 +106,8 @@ def _load():
         lib.tnref_row_counts.restype = None
         lib.tnref_argmax.argtypes = [_u32p, ctypes.c_uint64]
         lib.tnref_argmax.restype = ctypes.c_uint64
+        lib.tnref_splitmix64_stream.argtypes = [ctypes.c_uint64, ctypes.c_uint64, _u64p]
+        lib.tnref_splitmix64_stream.restype = None
         lib.tnref_hash_coeffs.argtypes = [ctypes.c_uint64, ctypes.c_uint32, _u64p]
         lib.tnref_hash_coeffs.restype = None
         lib.tnref_table_value.argtypes = [_u64p, ctypes.c_uint64]
@@ -243,6 +248,14 @@ def to_bool(S: np.ndarray, ncols: int) -> np.ndarray:
     bits = np.unpackbits(np.ascontiguousarray(S).view(np.uint8).reshape(S.shape[0], -1),
                          axis=1, bitorder="little")
     return bits[:, :ncols].astype(bool)
+
+
+def splitmix64_stream(state: int, count: int) -> np.ndarray:
+    """The first `count` outputs of SplitMix64 started at `state` (the generator
+    behind the hash coefficients and the HyperLogLog singletons)."""
+    out = np.zeros(count, dtype=np.uint64)
+    _load().tnref_splitmix64_stream(state, count, out)
+    return out
 
 
 def hash_coeffs(seed: int, replica: int) -> np.ndarray:

@@ -28,9 +28,11 @@
  *
  * Parity status: the component matrix, its sizes, the recombination and the
  * brute-force SI simulation are pinned by the tests (closed forms, brute force,
- * invariants).  The hash's exact constants are a project definition: its
- * structure and 4-wise independence are pinned, but agreement with the
- * authors' own (unpublished) hash values is "parity unpinned".
+ * invariants).  The hash's exact constants are a project definition: the
+ * SplitMix64 stream is pinned by the generator's known-answer values, the
+ * coefficient rule and the tables by big-integer restatements, and the
+ * structure and 4-wise independence by statistical tests.  Agreement with the
+ * authors' own (unpublished) hash values cannot be checked.
  */
 #include <math.h>
 #include <stdint.h>
@@ -395,6 +397,14 @@ static uint64_t splitmix64_next(uint64_t *state)
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
     return z ^ (z >> 31);
+}
+
+/* The first `count` outputs of the generator started at `state` (exported so
+ * that the tests can check it against the generator's known-answer values). */
+void tnref_splitmix64_stream(uint64_t state, uint64_t count, uint64_t *out)
+{
+    for (uint64_t i = 0; i < count; ++i)
+        out[i] = splitmix64_next(&state);
 }
 
 void tnref_hash_coeffs(uint64_t seed, uint32_t replica, uint64_t A[12])

@@ -292,6 +292,69 @@ def test_argmax_lowest_index():
 P61 = (1 << 61) - 1
 
 
+M64 = (1 << 64) - 1
+
+
+def test_splitmix64_known_answer():
+    """SplitMix64 (Steele, Lea and Flood, OOPSLA 2014; Vigna's reference C
+    implementation splitmix64.c) started at state 1234567 gives the sequence
+    below, the known-answer values that ports of the generator check in their
+    test suites.  A mistyped increment, multiplier or shift changes every one."""
+    want = [6457827717110365317, 3203168211198807973, 9817491932198370423,
+            4593380528125082431, 16408922859458223821]
+    assert [int(x) for x in oracle.splitmix64_stream(1234567, 5)] == want
+
+
+def _splitmix64_py(state, count):
+    """The published generator in Python integers: a Weyl step of the golden
+    gamma 0x9E3779B97F4A7C15, then the variant-13 finaliser (30, 27, 31)."""
+    out = []
+    for _ in range(count):
+        state = (state + 0x9E3779B97F4A7C15) & M64
+        z = state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M64
+        out.append(z ^ (z >> 31))
+    return out
+
+
+def test_splitmix64_matches_big_integer_generator():
+    assert _splitmix64_py(1234567, 5) == [int(x) for x in oracle.splitmix64_stream(1234567, 5)]
+    for state in (0, 1, 2**63, M64, 0xDEADBEEFCAFEF00D):
+        assert _splitmix64_py(state, 64) == [int(x) for x in oracle.splitmix64_stream(state, 64)]
+
+
+def test_hash_coeffs_match_big_integer_restatement():
+    """The coefficient rule (Section 4.1, with the reading of the unnamed rand
+    as SplitMix64 reduced mod 2^31 - 1): replica j's stream starts at
+    splitmix64(seed XOR j); A(i, c) = ((r1 << 32) + r2) mod p, drawn for
+    i = 0..2, c = 0..3, r1 before r2.  Written here in unbounded integers."""
+    for seed in (0, 1, 123, 2**40 + 7, M64):
+        for j in range(4):
+            stream = _splitmix64_py(seed ^ j, 1)[0]
+            draws = _splitmix64_py(stream, 24)
+            want = [(((draws[2 * q] % (2**31 - 1)) << 32) + draws[2 * q + 1] % (2**31 - 1)) % P61
+                    for q in range(12)]
+            assert [int(a) for a in oracle.hash_coeffs(seed, j)] == want
+
+
+def test_table_value_matches_big_integer_horner():
+    """T_i[x] = ((A0 x + A1) x + A2) x + A3 mod 2^61 - 1 (MultAddMod applied
+    order - 1 = 3 times), in unbounded integers, over coefficients anywhere in
+    the field (including p - 1) and every key size the hash uses (x < 2^17)."""
+    rng = np.random.default_rng(5)
+    rows = [[P61 - 1] * 4, [0, 0, 0, P61 - 1], [1, 0, 0, 0]]
+    rows += [[int(a) for a in rng.integers(0, P61, 4, dtype=np.uint64)] for _ in range(40)]
+    xs = [0, 1, 2, 65535, 65536, 131069, 131070] + [int(x) for x in rng.integers(0, 131071, 20)]
+    for A in rows:
+        arr = np.array(A, dtype=np.uint64)
+        for x in xs:
+            acc = A[0]
+            for c in range(1, 4):
+                acc = (acc * x + A[c]) % P61
+            assert oracle.table_value(arr, 0, x) == acc
+
+
 def test_hash_coefficients_in_field_and_distinct():
     A0 = oracle.hash_coeffs(123, 0)
     A1 = oracle.hash_coeffs(123, 1)
