@@ -184,19 +184,30 @@ typedef struct tn_plan tn_plan;
 typedef struct tn_plan_options {
     uint32_t window_events; /* target events per scheduling window (0 = default 640) */
     uint32_t slab_words;    /* 64-bit words of every row owned by one CTA when the
-                               plan is applied: an even number from 2 to 16
-                               (0 = default 16) */
+                               plan is applied: an even number from 2 to 128
+                               (0 = default 16).  Wide slabs (256-1024 byte row
+                               segments) suit large networks whose windows stream
+                               from global memory: fewer, longer DRAM bursts */
     uint32_t smem_rows;     /* row slots of the streaming kernel's shared-memory row
-                               buffer (at most 160 KB / (8 slab_words)); windows with
+                               buffer (at most 192 KB / (8 slab_words)); windows with
                                more rows (plus saved copies) stream from global
-                               memory (0 = 160 KB / (8 slab_words)).  A buffer small
+                               memory (0 = 160 KB / (8 slab_words) for slabs of up to
+                               16 words, 192 KB / (8 slab_words) above).  A buffer small
                                enough for two CTAs per SM (about 80 KB) runs two CTAs
                                of 4 consumer warps per SM; a larger one runs one CTA
                                of 12 consumer warps */
     uint32_t directed;      /* 1: event (u, v, t) is directed u -> v and only S[v] is
                                updated, S[v] |= S[u] (the paper's footnote to Section
                                3.1); timestamp groups stay snapshots.  0: undirected */
-    uint32_t reserved[4];   /* must be zero */
+    uint32_t wave_ctas;     /* 0: one CTA per slab_words-wide slab, ceil(row words /
+                               slab_words) CTAs per matrix.  N > 0: the row is
+                               spread over N CTAs of at most slab_words words each
+                               (two widths that differ by one unit; the unit is
+                               16 words, 128 bytes, when slab_words is a multiple
+                               of 16 and the row has at least N such units, else
+                               2 words), e.g. one full wave of the GPU's SMs.  N
+                               below ceil(row words / slab_words) is raised to it */
+    uint32_t reserved[3];   /* must be zero */
 } tn_plan_options;
 
 typedef struct tn_plan_stats {
@@ -602,14 +613,16 @@ tn_status tn_selftest_wait_timeout(void *stream);
 /* ---------------------------------------------------------------------------
  * tn_out_component_sizes_host -- the whole exact path from HOST arrays:
  * copies u, v, t (host, pinned or pageable) to the device, builds the
- * component matrix from the identity, computes the out-sizes and copies them
- * back.  out_sizes is a HOST uint32[n]; argmax a HOST uint32 or NULL.
- * Synchronous: returns when the host outputs are written.  Device memory is
- * taken from and returned to the stream-ordered allocator.
+ * component matrix from the identity (Algorithm 1, Section 3.1), computes the
+ * out-sizes (Section 3.3) and copies them back.  opt: plan options (window,
+ * slab width, row buffer, wave spread, direction; NULL = defaults), as for
+ * tn_plan_create.  out_sizes is a HOST uint32[n]; argmax a HOST uint32 or
+ * NULL.  Synchronous: returns when the host outputs are written.  Device
+ * memory is taken from and returned to the stream-ordered allocator.
  */
 tn_status tn_out_component_sizes_host(const uint32_t *u, const uint32_t *v, const int64_t *t,
-                                      uint64_t m, uint32_t n, uint32_t *out_sizes,
-                                      uint32_t *argmax, void *stream);
+                                      uint64_t m, uint32_t n, const tn_plan_options *opt,
+                                      uint32_t *out_sizes, uint32_t *argmax, void *stream);
 
 #ifdef __cplusplus
 }

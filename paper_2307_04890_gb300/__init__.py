@@ -56,7 +56,8 @@ class TnError(RuntimeError):
 
 class _Options(ctypes.Structure):
     _fields_ = [("window_events", ctypes.c_uint32), ("slab_words", ctypes.c_uint32),
-                ("smem_rows", ctypes.c_uint32), ("directed", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 4)]
+                ("smem_rows", ctypes.c_uint32), ("directed", ctypes.c_uint32), ("wave_ctas", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 3)]
 
 
 class _ErrorStats(ctypes.Structure):
@@ -137,7 +138,7 @@ def load_library(path: str | None = None):
         "tn_server_poll": ([vp, ctypes.POINTER(_JobRecord), u32, ctypes.POINTER(u32), u32], i32),
         "tn_server_get_stats": ([vp, ctypes.POINTER(_ServerStats)], i32),
         "tn_server_destroy": ([vp], i32),
-        "tn_out_component_sizes_host": ([vp, vp, vp, u64, u32, vp, vp, vp], i32),
+        "tn_out_component_sizes_host": ([vp, vp, vp, u64, u32, vp, vp, vp, vp], i32),
         "tn_grow_matrix": ([vp, u32, vp, u32, vp], i32),
         "tn_online_create": ([u32, ctypes.POINTER(_Options), vp, ctypes.POINTER(vp)], i32),
         "tn_online_push": ([vp, vp, vp, vp, u64, u32, vp], i32),
@@ -337,8 +338,13 @@ def tn_error_stats(est, exact, max_value: int, stream=None) -> dict:
     return {name: getattr(out, name) for name, _ in _ErrorStats._fields_}
 
 
-def tn_out_component_sizes_host(u, v, t, n: int):
-    """Whole exact path from host numpy arrays; returns (sizes uint32[n], argmax)."""
+def _plan_options(window_events=0, slab_words=0, smem_rows=0, directed=False, wave_ctas=0):
+    return _Options(window_events, slab_words, smem_rows, 1 if directed else 0, wave_ctas)
+
+
+def tn_out_component_sizes_host(u, v, t, n: int, **plan_options):
+    """Whole exact path from host numpy arrays; returns (sizes uint32[n], argmax).
+    ``plan_options``: window_events, slab_words, smem_rows, directed, wave_ctas."""
     import numpy as np
     lib = load_library()
     u = np.ascontiguousarray(u, dtype=np.uint32)
@@ -346,18 +352,20 @@ def tn_out_component_sizes_host(u, v, t, n: int):
     t = np.ascontiguousarray(t, dtype=np.int64)
     out = np.empty(n, dtype=np.uint32)
     am = np.zeros(1, dtype=np.uint32)
+    opt = _plan_options(**plan_options)
     _check(lib.tn_out_component_sizes_host(u.ctypes.data, v.ctypes.data, t.ctypes.data, len(u), n,
-                                           out.ctypes.data, am.ctypes.data, _stream()),
+                                           ctypes.byref(opt), out.ctypes.data, am.ctypes.data, _stream()),
            "tn_out_component_sizes_host")
     return out, int(am[0])
 
 
 def tn_out_component_sizes_host_ptrs(u_ptr: int, v_ptr: int, t_ptr: int, m: int, n: int, out_ptr: int,
-                                     argmax_ptr: int | None = None, stream=None):
+                                     argmax_ptr: int | None = None, stream=None, **plan_options):
     """Same as ``tn_out_component_sizes_host`` on raw host pointers (pinned buffers)."""
     lib = load_library()
-    _check(lib.tn_out_component_sizes_host(u_ptr, v_ptr, t_ptr, m, n, out_ptr, argmax_ptr, _stream(stream)),
-           "tn_out_component_sizes_host")
+    opt = _plan_options(**plan_options)
+    _check(lib.tn_out_component_sizes_host(u_ptr, v_ptr, t_ptr, m, n, ctypes.byref(opt), out_ptr, argmax_ptr,
+                                           _stream(stream)), "tn_out_component_sizes_host")
 
 
 class _OnlineState(ctypes.Structure):
@@ -370,12 +378,12 @@ class Plan:
     """A validated, scheduled event batch (tn_plan_create / tn_plan_apply)."""
 
     def __init__(self, u, v, t, n: int, t_after=None, window_events: int = 0, slab_words: int = 0,
-                 smem_rows: int = 0, directed: bool = False, stream=None):
+                 smem_rows: int = 0, directed: bool = False, wave_ctas: int = 0, stream=None):
         lib = load_library()
         self.m = _events(u, v, t)
         self.n = n
         self.device = u.device
-        opt = _Options(window_events, slab_words, smem_rows, 1 if directed else 0)
+        opt = _Options(window_events, slab_words, smem_rows, 1 if directed else 0, wave_ctas)
         h = ctypes.c_void_p()
         if t_after is not None:
             _dev(t_after, ("int64",), "t_after")
@@ -507,7 +515,7 @@ def tn_autotune(u, v, t, n: int, replicas: int = 1, sample_events: int = 200_000
     _check(lib.tn_autotune(_ptr(u), _ptr(v), _ptr(t), m, n, ncols, replicas, sample_events, _stream(stream),
                            ctypes.byref(res)), "tn_autotune")
     return {"window_events": res.best.window_events, "slab_words": res.best.slab_words,
-            "smem_rows": res.best.smem_rows, "best_ms": res.best_ms, "tried": res.tried,
+            "smem_rows": res.best.smem_rows, "wave_ctas": res.best.wave_ctas, "best_ms": res.best_ms, "tried": res.tried,
             "cached": bool(res.cached), "sample_events": res.sample_events}
 
 
@@ -605,9 +613,9 @@ class Online:
     may be added between batches."""
 
     def __init__(self, n: int, window_events: int = 0, slab_words: int = 0, smem_rows: int = 0,
-                 directed: bool = False, stream=None):
+                 directed: bool = False, wave_ctas: int = 0, stream=None):
         lib = load_library()
-        opt = _Options(window_events, slab_words, smem_rows, 1 if directed else 0)
+        opt = _Options(window_events, slab_words, smem_rows, 1 if directed else 0, wave_ctas)
         h = ctypes.c_void_p()
         _check(lib.tn_online_create(n, ctypes.byref(opt), _stream(stream), ctypes.byref(h)), "tn_online_create")
         self._h = h

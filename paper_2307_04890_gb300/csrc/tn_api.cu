@@ -65,8 +65,8 @@ extern "C" uint64_t tn_row_words(uint64_t ncols) { return ((ncols + 1023) / 1024
 // Whole exact path from host arrays: H2D copy of the events, component matrix
 // from the identity (Algorithm 1), out-sizes (Section 3.1), D2H copy.
 extern "C" tn_status tn_out_component_sizes_host(const uint32_t *u, const uint32_t *v, const int64_t *t,
-                                                 uint64_t m, uint32_t n, uint32_t *out_sizes, uint32_t *argmax,
-                                                 void *stream)
+                                                 uint64_t m, uint32_t n, const tn_plan_options *opt,
+                                                 uint32_t *out_sizes, uint32_t *argmax, void *stream)
 {
     if (!out_sizes || n == 0 || n >= (1u << 30) || (m > 0 && (!u || !v || !t))) return TN_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
@@ -89,7 +89,16 @@ extern "C" tn_status tn_out_component_sizes_host(const uint32_t *u, const uint32
         if ((err = cudaMemcpyAsync(dv, v, m * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess) goto fail;
         if ((err = cudaMemcpyAsync(dt, t, m * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess) goto fail;
     }
-    rc = tn_component_matrix(du, dv, dt, m, n, S, nullptr, TN_INIT_IDENTITY, stream);
+    if (m == 0) {
+        rc = tn_init_matrix(S, n, n, nullptr, stream);
+    } else {
+        tn_plan *plan = nullptr;
+        rc = tn_plan_create(du, dv, dt, m, n, nullptr, opt, stream, &plan);
+        if (rc == TN_OK) {
+            rc = tn_plan_apply(plan, S, n, nullptr, nullptr, TN_INIT_IDENTITY, stream);
+            tn_plan_destroy(plan, stream);
+        }
+    }
     if (rc == TN_OK) rc = tn_out_sizes(S, n, n, dout, nullptr, argmax ? dam : nullptr, stream);
     if (rc == TN_OK) {
         if ((err = cudaMemcpyAsync(out_sizes, dout, (uint64_t)n * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess)

@@ -32,7 +32,8 @@ constexpr int kWarpsShared = 4;
 constexpr int kMaxThreads = 32 * kWarpsAlone + 32;
 constexpr int kStages = 2;
 constexpr uint32_t kEndItem = 0xFFFFFFFFu;
-constexpr int kMaxJobs = 24;
+constexpr int kMaxPlans = 24;  // networks per launch
+constexpr int kMaxJobs = 2 * kMaxPlans;  // a network spread over a wave has CTAs of two widths
 
 struct Job {
     const uint2 *blob;
@@ -43,7 +44,8 @@ struct Job {
     uint64_t ld;    // row stride in words
     uint64_t *tmp;  // saved-row slots of global windows, ld words each
     int32_t *status;
-    uint32_t sw;    // slab words per CTA (even, 2..16)
+    uint64_t w_begin;  // first row word of the job's first CTA
+    uint32_t sw;    // slab words per CTA (even, 2..kMaxSlabWords)
     uint32_t cpr;   // 16-byte chunks of a row segment = sw / 2
     uint32_t cta_begin;
     uint32_t dcap;  // row slots of the shared-memory row buffer
@@ -204,58 +206,146 @@ __device__ inline void apply_tile_direct(const Job &J, const uint2 *ops, uint32_
     }
 }
 
-// Ops of one level are independent: the row segments of a chunk of them are
-// first copied into shared memory (private slots 2i and 2i+1 for op i, so no
-// lookup is needed and every copy is in flight at once), then each op's
-// result goes from registers straight to its destination rows.
+// Ops of one level are independent.  Each consumer thread takes the ops
+// lane0, lane0 + stride, ... of the tile and runs them through a private ring
+// of kRing op slots in shared memory (two row chunks per op): the copies of
+// the op kRing - 1 places ahead are issued (cp.async, one commit group per op)
+// before the current op's rows are read back, combined and stored from
+// registers.  A thread reads only the slots it filled itself, so no barrier is
+// needed inside a tile; the item loop's barrier orders one level's stores
+// before the next level's loads.
+constexpr int kRing = 8;
+
+__device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ inline void cp_async_wait_group()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+__device__ inline void red_or16(uint64_t *p, u64x2 v)
+{
+    asm volatile("red.global.or.b64 [%0], %1;" ::"l"(p), "l"(v.x) : "memory");
+    asm volatile("red.global.or.b64 [%0], %1;" ::"l"(p + 1), "l"(v.y) : "memory");
+}
+
+// The thread's PULLs, S[x] |= OR of the listed source rows, as a flat sequence
+// of (x, source) pairs through the same private ring: a source chunk is copied
+// in kRing - 1 pairs ahead, then ORed into row x by a reduction at L2
+// (red.global.or), so x is never loaded and the pairs of one PULL need no
+// order among themselves (OR is associative and commutative).  Rows written
+// by a PULL are read by no other op of the same level.
+struct PullCursor {
+    uint32_t o, q, c;  // op index, next source (0-based), source count
+};
+
+__device__ inline void pull_cursor_seek(PullCursor &cur, const Job &J, const uint2 *ops, uint32_t count,
+                                        uint32_t stride)
+{
+    while (cur.o < count && cur.q >= cur.c) {
+        cur.o += stride;
+        while (cur.o < count && (ops[cur.o].x >> kKindShift) != kPull) cur.o += stride;
+        cur.q = 0;
+        cur.c = cur.o < count ? __ldg(J.aux + ops[cur.o].y) : 0u;
+    }
+}
+
+__device__ inline void apply_pulls_ring(const Job &J, const uint2 *ops, uint32_t count, u64x2 *mine, const Lane &L)
+{
+    const uint32_t cpr = L.cpr, stride = L.stride;
+    const uint64_t col = L.col;
+    PullCursor in{L.lane0, 0u, 0u};
+    while (in.o < count && (ops[in.o].x >> kKindShift) != kPull) in.o += stride;
+    if (in.o >= count) return;
+    in.c = __ldg(J.aux + ops[in.o].y);
+    pull_cursor_seek(in, J, ops, count, stride);
+    PullCursor out = in;
+    uint32_t issued = 0, done = 0;
+    auto issue = [&]() {
+        if (in.o >= count) return;
+        const uint32_t ref = __ldg(J.aux + ops[in.o].y + 1 + in.q);
+        const uint32_t q = L.lane0 + (issued % kRing) * stride;
+        cp_async16(mine + (2 * q) * cpr, row_ptr(J, ref, col));
+        ++issued;
+        ++in.q;
+        pull_cursor_seek(in, J, ops, count, stride);
+    };
+#pragma unroll 1
+    for (uint32_t k = 0; k < kRing - 1; ++k) {
+        issue();
+        cp_async_commit();
+    }
+#pragma unroll 1
+    while (done < issued) {
+        issue();
+        cp_async_commit();
+        cp_async_wait_group<kRing - 1>();  // pair `done` has landed
+        const uint32_t q = L.lane0 + (done % kRing) * stride;
+        red_or16(J.S + (uint64_t)(ops[out.o].x & kIdMask) * J.ld + col, lds16(mine + (2 * q) * cpr));
+        ++done;
+        ++out.q;
+        pull_cursor_seek(out, J, ops, count, stride);
+    }
+    cp_async_wait_group<0>();
+}
+
 template <bool kMax>
 __device__ inline void apply_tile(const Job &J, const uint2 *ops, uint32_t count, u64x2 *buf, uint32_t dcap,
                                   const Lane &L)
 {
     const uint32_t cpr = L.cpr, stride = L.stride;
     const uint64_t col = L.col;
-    if (dcap < 64) {
+    if (dcap < 2u * kRing * stride) {
         apply_tile_direct<kMax>(J, ops, count, L);
         return;
     }
-    const uint32_t chunk_ops = dcap / 2;
-    u64x2 *mine = buf + L.chunk;
-    for (uint32_t c0 = 0; c0 < count; c0 += chunk_ops) {
-        const uint32_t cn = count - c0 < chunk_ops ? count - c0 : chunk_ops;
-        if (L.active) {
-            for (uint32_t i = L.lane0; i < cn; i += stride) {
-                const uint2 op = ops[c0 + i];
-                const uint32_t kind = op.x >> kKindShift;
-                if (kind == kPull) continue;
-                if (kind != kCopy) cp_async16(mine + (2 * i) * cpr, J.S + (uint64_t)(op.x & kIdMask) * J.ld + col);
-                cp_async16(mine + (2 * i + 1) * cpr, J.S + (uint64_t)op.y * J.ld + col);
-            }
-        }
-        cp_async_wait_all();
-        consumers_sync();
-        if (L.active) {
-            for (uint32_t i = L.lane0; i < cn; i += stride) {
-                const uint2 op = ops[c0 + i];
-                const uint32_t kind = op.x >> kKindShift;
-                if (kind == kPull) continue;
-                const uint64_t ia = (uint64_t)(op.x & kIdMask) * J.ld + col;
-                const u64x2 rb = lds16(mine + (2 * i + 1) * cpr);
-                if (kind == kCopy) {
-                    st_row16(J.tmp + ia, rb);
-                } else {
-                    const u64x2 r = combine16<kMax>(lds16(mine + (2 * i) * cpr), rb);
-                    st_row16(J.S + ia, r);
-                    if (kind == kEvent) st_row16(J.S + (uint64_t)op.y * J.ld + col, r);
-                }
-            }
-        }
-        consumers_sync();  // the slots are reused by the next chunk
-    }
     if (!L.active) return;
+    u64x2 *mine = buf + L.chunk;
+    const uint32_t nk = count > L.lane0 ? (count - L.lane0 + stride - 1) / stride : 0;
+    // ring slot r of this thread holds its op's rows in slots 2q, 2q + 1, q = lane0 + r * stride
+    auto issue = [&](uint32_t k) {
+        const uint2 op = ops[L.lane0 + k * stride];
+        const uint32_t kind = op.x >> kKindShift;
+        const uint32_t q = L.lane0 + (k % kRing) * stride;
+        if (kind != kPull) {
+            if (kind != kCopy) cp_async16(mine + (2 * q) * cpr, J.S + (uint64_t)(op.x & kIdMask) * J.ld + col);
+            cp_async16(mine + (2 * q + 1) * cpr, J.S + (uint64_t)op.y * J.ld + col);
+        }
+    };
+#pragma unroll 1
+    for (uint32_t k = 0; k < kRing - 1; ++k) {
+        if (k < nk) issue(k);
+        cp_async_commit();
+    }
+#pragma unroll 1
+    for (uint32_t k = 0; k < nk; ++k) {
+        if (k + kRing - 1 < nk) issue(k + kRing - 1);
+        cp_async_commit();
+        cp_async_wait_group<kRing - 1>();  // op k's copies have landed
+        const uint2 op = ops[L.lane0 + k * stride];
+        const uint32_t kind = op.x >> kKindShift;
+        if (kind == kPull) continue;
+        const uint32_t q = L.lane0 + (k % kRing) * stride;
+        const uint64_t ia = (uint64_t)(op.x & kIdMask) * J.ld + col;
+        const u64x2 rb = lds16(mine + (2 * q + 1) * cpr);
+        if (kind == kCopy) {
+            st_row16(J.tmp + ia, rb);
+        } else {
+            const u64x2 r = combine16<kMax>(lds16(mine + (2 * q) * cpr), rb);
+            st_row16(J.S + ia, r);
+            if (kind == kEvent) st_row16(J.S + (uint64_t)op.y * J.ld + col, r);
+        }
+    }
+    cp_async_wait_group<0>();
     // multi-source updates of tie groups (hub rows) in a second pass
-    for (uint32_t o = L.lane0; o < count; o += stride) {
-        const uint2 op = ops[o];
-        if ((op.x >> kKindShift) == kPull) apply_pull<kMax>(J, op.x & kIdMask, op.y, col);
+    if (kMax) {
+        for (uint32_t o = L.lane0; o < count; o += stride) {
+            const uint2 op = ops[o];
+            if ((op.x >> kKindShift) == kPull) apply_pull<kMax>(J, op.x & kIdMask, op.y, col);
+        }
+    } else {
+        apply_pulls_ring(J, ops, count, mine, L);
     }
 }
 
@@ -353,7 +443,7 @@ __global__ void __launch_bounds__(kMaxThreads) stream_kernel(const __grid_consta
     __shared__ int32_t gate;
 
     const Job &J = jl.job[find_job(jl, blockIdx.x)];
-    const uint64_t w0 = (uint64_t)(blockIdx.x - J.cta_begin) * J.sw;
+    const uint64_t w0 = J.w_begin + (uint64_t)(blockIdx.x - J.cta_begin) * J.sw;
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
     if (threadIdx.x == 0) {
         gate = *(volatile int32_t *)J.status;  // an earlier error gates this job
@@ -531,6 +621,36 @@ __global__ void set_t_last_kernel(const int64_t *tb, int64_t *t_last, const int3
     if (*(volatile const int32_t *)status == 0) *t_last = tb[1];
 }
 
+// Column slabs of one matrix of `ld` row words: ceil(ld / sw) CTAs of sw
+// words, or -- with wave > 0 -- exactly max(wave, ceil(ld / sw)) CTAs of two
+// widths that differ by one unit (16 words when sw is a multiple of 16 and the
+// row holds that many units, else 2 words): the wider ones first.
+struct SlabSplit {
+    uint64_t w_begin;
+    uint32_t sw, ctas;
+};
+
+static int split_slabs(uint64_t ld, uint32_t sw, uint32_t wave, SlabSplit out[2])
+{
+    const uint64_t plain = (ld + sw - 1) / sw;
+    if (wave == 0 || ld == 0) {
+        out[0] = SlabSplit{0, sw, (uint32_t)plain};
+        return 1;
+    }
+    const uint64_t C = wave > plain ? wave : plain;
+    const uint32_t unit = (sw % 16 == 0 && ld / 16 >= C) ? 16u : 2u;
+    const uint64_t units = ld / unit;  // ld is a multiple of 16
+    if (units <= C) {  // no more CTAs than units: one unit each
+        out[0] = SlabSplit{0, unit, (uint32_t)units};
+        return 1;
+    }
+    const uint64_t q = units / C, r = units % C;
+    int k = 0;
+    if (r) out[k++] = SlabSplit{0, (uint32_t)((q + 1) * unit), (uint32_t)r};
+    out[k++] = SlabSplit{r * (q + 1) * unit, (uint32_t)(q * unit), (uint32_t)(C - r)};
+    return k;
+}
+
 static int grid_for(uint64_t work)
 {
     uint64_t g = (work + 255) / 256;
@@ -550,12 +670,12 @@ tn_status apply_jobs(const tn_plan *const *plans, uint64_t *const *S, const uint
         if ((flags & TN_INIT_IDENTITY) && !src[i] && ncols[i] != p->n) return TN_EINVAL;
     }
     const size_t smem_base = (size_t)kStages * kStageBytes + 2 * kStages * sizeof(uint64_t) + kStages * sizeof(StageHdr);
-    uint64_t *tmps[kMaxJobs];
-    for (uint32_t base = 0; base < count; base += kMaxJobs) {
-        const uint32_t nj = count - base < (uint32_t)kMaxJobs ? count - base : (uint32_t)kMaxJobs;
+    uint64_t *tmps[kMaxPlans];
+    for (uint32_t base = 0; base < count; base += kMaxPlans) {
+        const uint32_t nj = count - base < (uint32_t)kMaxPlans ? count - base : (uint32_t)kMaxPlans;
         JobList jl;
         memset(&jl, 0, sizeof(jl));
-        jl.count = nj;
+        jl.count = 0;
         uint32_t ctas = 0;
         size_t smem = smem_base;
         for (uint32_t j = 0; j < nj; ++j) {
@@ -580,23 +700,27 @@ tn_status apply_jobs(const tn_plan *const *plans, uint64_t *const *S, const uint
                 }
             }
             if (p->temps) TN_CUDA_TRY(cudaMallocAsync((void **)&tmps[j], p->temps * ld * sizeof(uint64_t), st));
-            const uint32_t sw = p->slab_words;
-            const size_t need = smem_base + (size_t)p->dcap * sw * 8;
+            const size_t need = smem_base + (size_t)p->dcap * p->slab_words * 8;
             if (need > smem) smem = need;
-            Job &J = jl.job[j];
-            J.blob = p->d_blob;
-            J.items = p->d_items;
-            J.aux = p->d_aux;
-            J.nitems = p->items;
-            J.S = S[i];
-            J.ld = ld;
-            J.tmp = tmps[j];
-            J.status = p->d_status;
-            J.sw = sw;
-            J.cpr = sw / 2;
-            J.dcap = p->dcap;
-            J.cta_begin = ctas;
-            ctas += (uint32_t)((ld + sw - 1) / sw);
+            SlabSplit sp[2];
+            const int parts = split_slabs(ld, p->slab_words, p->wave_ctas, sp);
+            for (int k = 0; k < parts; ++k) {
+                Job &J = jl.job[jl.count++];
+                J.blob = p->d_blob;
+                J.items = p->d_items;
+                J.aux = p->d_aux;
+                J.nitems = p->items;
+                J.S = S[i];
+                J.ld = ld;
+                J.tmp = tmps[j];
+                J.status = p->d_status;
+                J.w_begin = sp[k].w_begin;
+                J.sw = sp[k].sw;
+                J.cpr = sp[k].sw / 2;
+                J.dcap = p->dcap;
+                J.cta_begin = ctas;
+                ctas += sp[k].ctas;
+            }
         }
         TN_CUDA_TRY(cudaGetLastError());
         if (ctas) {

@@ -103,7 +103,9 @@ namespace {
 std::mutex g_tune_mu;
 std::map<std::tuple<int, uint32_t, uint32_t, uint32_t, int>, tn_tune_result> g_tune_cache;
 
-constexpr uint64_t kTuneBytesLimit = 4ull << 30;  // scratch matrices of one timing run
+constexpr uint64_t kTuneBytesCap = 64ull << 30;  // scratch matrices of one timing run: at most this,
+                                                 // and at most half of the free device memory
+constexpr uint32_t kTuneWidest = 64;             // widest slab tried
 
 // Time of one batched application of `plan` to `count` matrices of `ncols`
 // columns (the first ncols node ids as sources when ncols < n), best of 2.
@@ -169,8 +171,11 @@ extern "C" tn_status tn_autotune(const uint32_t *u, const uint32_t *v, const int
     const uint64_t msample = sample_events && sample_events < m ? sample_events : m;
     out->sample_events = msample;
 
+    size_t free_b = 0, total_b = 0;
+    TN_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+    const uint64_t kTuneBytesLimit = free_b / 2 < kTuneBytesCap ? free_b / 2 : kTuneBytesCap;
     // source ids 0..max-1 for column-subset timings
-    const uint32_t max_cols = (uint32_t)nsm * 2u * 16u * 64u;
+    const uint32_t max_cols = (uint32_t)nsm * 2u * kTuneWidest * 64u;
     uint32_t *ids = nullptr;
     std::vector<uint32_t> hids(max_cols);
     for (uint32_t i = 0; i < max_cols; ++i) hids[i] = i;
@@ -178,14 +183,17 @@ extern "C" tn_status tn_autotune(const uint32_t *u, const uint32_t *v, const int
     TN_CUDA_TRY(cudaMemcpyAsync(ids, hids.data(), max_cols * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
     TN_CUDA_TRY(cudaStreamSynchronize(st));
 
-    const uint32_t slabs[] = {2, 4, 8, 12, 16};
+    // slabs above 16 words (256- to 512-byte row segments, 192 KB row buffer)
+    // suit large networks whose windows stream from global memory; they run one
+    // CTA per SM
+    const uint32_t slabs[] = {2, 4, 8, 12, 16, 24, 32, 48, kTuneWidest};
     const uint32_t windows[] = {320, 640, 1024};
     float best = INFINITY;
     tn_status rc = TN_OK;
     for (uint32_t sw : slabs) {
         if (sw > ld || rc != TN_OK) continue;
-        for (int half = 0; half < 2 && rc == TN_OK; ++half) {
-            const uint64_t occ = half ? 2 : 1;  // 32 KB of stages + 80 or 160 KB of rows per CTA
+        for (int half = 0; half < (sw <= 16 ? 2 : 1) && rc == TN_OK; ++half) {
+            const uint64_t occ = half ? 2 : 1;  // 32 KB of stages + 80 or 160 (192) KB of rows per CTA
             const uint64_t per_rep = (ld + sw - 1) / sw;
             const uint64_t total = per_rep * replicas;
             const uint64_t slots = (uint64_t)nsm * occ;
@@ -222,7 +230,7 @@ extern "C" tn_status tn_autotune(const uint32_t *u, const uint32_t *v, const int
                 memset(&opt, 0, sizeof(opt));
                 opt.window_events = win;
                 opt.slab_words = sw;
-                opt.smem_rows = (half ? 80u : 160u) * 1024u / (8u * sw);
+                opt.smem_rows = (half ? 80u : (sw <= 16 ? 160u : 192u)) * 1024u / (8u * sw);
                 tn_plan *plan = nullptr;
                 rc = tn_plan_create(u, v, t, msample, n, nullptr, &opt, st, &plan);
                 if (rc != TN_OK) break;

@@ -66,6 +66,8 @@ constexpr uint32_t kItemLevelEnd = 2u;
 constexpr uint32_t kLocalBits = 14;
 constexpr uint32_t kLocalMask = 0x3FFFu;
 constexpr uint32_t kLocalSlotLimit = 0x3FFFu;  // above the 10,240 slots a 160 KB row buffer can hold
+// Widest column slab of one CTA: 128 words (1 KB row segments).
+constexpr uint32_t kMaxSlabWords = 128;
 constexpr uint32_t kLastA = 1u << 29;
 constexpr uint32_t kLastB = 1u << 28;
 
@@ -242,7 +244,8 @@ struct tn_plan {
     uint32_t n;
     uint64_t windows, levels, ops, aux, temps, big_windows, local_windows, items, blob8;
     int64_t t_first, t_last;
-    uint32_t slab_words;  // 64-bit words of every row owned by one CTA
+    uint32_t slab_words;  // 64-bit words of every row owned by one CTA (the widest, with wave_ctas)
+    uint32_t wave_ctas;   // 0, or the number of CTAs one matrix is spread over
     uint32_t dcap;        // row slots of the kernel's shared-memory row buffer
     uint2 *d_blob;        // [blob8 + 2]  item payloads (8-byte units)
     uint4 *d_items;       // [items]      work items in execution order

@@ -42,7 +42,8 @@ namespace tn {
 constexpr int kPlanThreads = 256;
 constexpr uint32_t kDefaultWindow = 640;
 constexpr uint32_t kDefaultSlab = 16;
-constexpr uint32_t kRowBufferBytes = 160 * 1024;  // default shared-memory row buffer of the streaming kernel
+constexpr uint32_t kRowBufferBytes = 160 * 1024;  // default shared-memory row buffer, slabs of up to 16 words
+constexpr uint32_t kRowBufferWide = 192 * 1024;   // default (and largest) row buffer for wider slabs
 constexpr uint32_t kWinFields = 8;  // nops, nlev, naux, ntemp, local, blob8, nitems, all ops
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 constexpr uint32_t kNone = 0xFFFFFFFFu;
@@ -755,20 +756,21 @@ extern "C" tn_status tn_plan_create(const uint32_t *u, const uint32_t *v, const 
     if (!plan_out) return TN_EINVAL;
     *plan_out = nullptr;
     if (!u || !v || !t || m == 0 || n == 0 || n >= (1u << 30) || m >= (1ull << 30)) return TN_EINVAL;
-    uint32_t sw = kDefaultSlab, window = kDefaultWindow, rows = 0;
+    uint32_t sw = kDefaultSlab, window = kDefaultWindow, rows = 0, wave = 0;
     if (opt) {
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < 3; ++i)
             if (opt->reserved[i]) return TN_EINVAL;
         if (opt->directed > 1) return TN_EINVAL;
         if (opt->slab_words) sw = opt->slab_words;
         if (opt->window_events) window = opt->window_events;
         rows = opt->smem_rows;
+        wave = opt->wave_ctas;
     }
-    if (sw < 2 || sw > 16 || (sw & 1u)) return TN_EINVAL;  // even: whole 16-byte chunks
+    if (sw < 2 || sw > kMaxSlabWords || (sw & 1u)) return TN_EINVAL;  // even: whole 16-byte chunks
     if (window < 32) window = 32;
-    if (rows == 0) rows = kRowBufferBytes / (sw * 8);
+    if (rows == 0) rows = (sw <= 16 ? kRowBufferBytes : kRowBufferWide) / (sw * 8);
     if (rows > kLocalSlotLimit) rows = kLocalSlotLimit;
-    if ((uint64_t)rows * sw * 8 > 160 * 1024) return TN_EINVAL;  // row buffer must fit the kernel's shared memory
+    if ((uint64_t)rows * sw * 8 > kRowBufferWide) return TN_EINVAL;  // row buffer must fit the kernel's shared memory
     cudaStream_t st = (cudaStream_t)stream;
     tn_internal_keep_pool();
 
@@ -794,6 +796,7 @@ extern "C" tn_status tn_plan_create(const uint32_t *u, const uint32_t *v, const 
     p->n = n;
     p->windows = a.nw;
     p->slab_words = sw;
+    p->wave_ctas = wave;
     p->dcap = rows;
 
     tn_status rc = TN_OK;

@@ -1,8 +1,13 @@
-"""The N > 1 path of bench.py on CPU (gloo, world size 2).
+"""The N > 1 paths of bench.py on CPU (gloo, world size 2).
 
-Ranks run independent replicas of the workload (different seeds, no data-path
-collective); the job's time is the slowest rank's (all-reduce MAX); under
-torchrun only rank 0 of the reference arm prints its line.
+The exact workloads split the source columns over the ranks (columns never
+interact, Section 3.1): every rank streams all events over its own block of
+columns and the out-sizes are all-gathered, with the largest out-component
+taken over the gathered sizes.  Here each rank computes its block with the
+oracle and runs bench.py's gather.  The hashed and online workloads run
+independent replicas (different seeds); the job's time is the slowest rank's
+(all-reduce MAX); under torchrun only rank 0 of the reference arm prints its
+line.
 """
 import json
 import os
@@ -35,6 +40,62 @@ def _rank_main(rank, world, port, out_dir):
         json.dump({"slowest": slowest, "seed": bench.replica_seed(bench.WORKLOADS["uniform-small"], rank)}, f)
     dist.barrier()
     dist.destroy_process_group()
+
+
+def _split_rank_main(rank, world, port, out_dir):
+    import torch
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle
+
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    w = bench.WORKLOADS["uniform-small"]
+    u, v, t = bench.make_events(w)  # the same events on every rank
+    n = w["n"]
+    c0, c1 = bench.column_range(n, rank, world)
+    S = oracle.component_matrix(u, v, t, n, src=np.arange(c0, c1, dtype=np.uint32))
+    local = torch.from_numpy(oracle.column_counts(S, c1 - c0).astype(np.int32))
+    full, am = bench.gather_sizes(local, n, rank, world, dist)
+    np.save(os.path.join(out_dir, f"sizes{rank}.npy"), full.numpy())
+    with open(os.path.join(out_dir, f"split{rank}.json"), "w") as f:
+        json.dump({"argmax": am, "c0": c0, "c1": c1}, f)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_column_split_gathers_the_whole_matrix_sizes(tmp_path, world):
+    """n = 1,000, m = 20,000 (the uniform small workload): the gathered sizes
+    and the argmax equal the oracle's on the whole matrix, on every rank."""
+    import torch.multiprocessing as mp
+    import oracle
+
+    port = free_port()
+    mp.start_processes(_split_rank_main, args=(world, port, str(tmp_path)), nprocs=world, join=True,
+                       start_method="spawn")
+    sys.path.insert(0, ROOT)
+    import bench
+    w = bench.WORKLOADS["uniform-small"]
+    u, v, t = bench.make_events(w)
+    want = oracle.column_counts(oracle.component_matrix(u, v, t, w["n"]), w["n"])
+    blocks = []
+    for r in range(world):
+        rec = json.load(open(tmp_path / f"split{r}.json"))
+        assert np.array_equal(np.load(tmp_path / f"sizes{r}.npy").view(np.uint32), want)
+        assert rec["argmax"] == oracle.argmax(want)
+        blocks.append((rec["c0"], rec["c1"]))
+    assert blocks[0][0] == 0 and blocks[-1][1] == w["n"]
+    assert all(a[1] == b[0] and a[0] < a[1] for a, b in zip(blocks, blocks[1:]))
+
+
+def test_gather_breaks_size_ties_by_lowest_id():
+    import torch
+    sys.path.insert(0, ROOT)
+    import bench
+    sizes = torch.tensor([3, 9, 2, 9, 9], dtype=torch.int32)
+    full, am = bench.gather_sizes(sizes, 5, 0, 1, None)
+    assert am == 1 and torch.equal(full, sizes)
 
 
 def test_two_gloo_ranks_max_time_and_distinct_replicas(tmp_path):

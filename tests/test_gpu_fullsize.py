@@ -59,7 +59,7 @@ def check_matrix_properties(S, n):
 
 def test_activity_n1e5_m1e7_bench_config():
     n, m = 100_000, 10_000_000
-    u, v, t = synth.activity_driven(n, m, seed=2)  # the bench's default workload
+    u, v, t = synth.activity_driven(n, m, seed=2)  # bench.py --workload activity
     du, dv, dt = dev(u), dev(v), dev(t, np.int64)
     plan = tn.Plan(du, dv, dt, n)  # default options, as timed by bench.py
     S = torch.empty((n, tn.tn_row_words(n)), dtype=torch.int64, device="cuda")
@@ -75,11 +75,13 @@ def test_activity_n1e5_m1e7_bench_config():
 
 def test_bursty_n5e5_m1e8_bench_config():
     n, m = 500_000, 100_000_000
-    u, v, t = synth.powerlaw_bursty(n, m, seed=3)
+    u, v, t = synth.powerlaw_bursty(n, m, seed=3)  # bench.py's default workload
     du, dv, dt = dev(u), dev(v), dev(t, np.int64)
-    plan = tn.Plan(du, dv, dt, n)
+    # the plan options bench.py times: the autotuner's choice on the first 2e6 events
+    tuned = tn.tn_autotune(du, dv, dt, n, sample_events=2_000_000)
+    plan = tn.Plan(du, dv, dt, n, **{k: tuned[k] for k in ("window_events", "slab_words", "smem_rows")})
     st = plan.stats()
-    assert st["big_windows"] > 0  # tie groups larger than a window
+    assert st["big_windows"] > 0 and st["local_windows"] == 0  # every tie group is larger than a window
     S = torch.empty((n, tn.tn_row_words(n)), dtype=torch.int64, device="cuda")
     tn.tn_init_matrix(S, n)
     plan.apply(S)

@@ -134,6 +134,74 @@ def test_local_and_global_windows_identical(smem_rows, slab):
     assert np.array_equal(host_matrix(S, n), oracle.component_matrix(u, v, t, n))
 
 
+@pytest.mark.parametrize("slab", [18, 26, 40, 52, 64])
+@pytest.mark.parametrize("smem_rows", [1, 0])
+def test_wide_slabs_identical(slab, smem_rows):
+    """Slabs wider than 16 words (up to 512-byte row segments) with the 192 KB
+    row buffer: three or more CTAs per row, the last one ragged (141 row words,
+    stride 144), through the direct global-memory path (smem_rows=1: a buffer
+    too small for the ring) and through shared-memory records (default)."""
+    n = 9000
+    u, v, t = synth.uniform_events(n, 60_000, t_range=20_000, seed=21)
+    du, dv, dt = dev_events(u, v, t)
+    plan = tn.Plan(du, dv, dt, n, window_events=200, slab_words=slab, smem_rows=smem_rows)
+    st = plan.stats()
+    assert (st["local_windows"] == 0) == (smem_rows == 1)
+    S = torch.empty((n, tn.tn_row_words(n)), dtype=torch.int64, device="cuda")
+    plan.apply(S, init=True)
+    assert plan.status() == 0
+    assert np.array_equal(host_matrix(S, n), oracle.component_matrix(u, v, t, n))
+
+
+@pytest.mark.parametrize("slab", [16, 26, 52])
+def test_bursty_big_windows_global_ring(slab):
+    """Power-law degrees and Pareto gaps rounded to seconds (tie groups of
+    about 120 events, hub nodes), in windows of 3,000 events: a window touches
+    more rows than the row buffer holds, so it streams from global memory
+    through the per-thread ring of copies (the buffer holds at least 16 slots
+    per row group: 1,280 >= 16 * 48 at 16 words, 945 >= 16 * 29 at 26 words,
+    472 >= 16 * 14 at 52 words), then applies the hub PULLs."""
+    n = 20_000
+    u, v, t = synth.powerlaw_bursty(n, 400_000, seed=9)
+    du, dv, dt = dev_events(u, v, t)
+    plan = tn.Plan(du, dv, dt, n, window_events=3000, slab_words=slab)
+    st = plan.stats()
+    assert st["local_windows"] * 10 <= st["windows"] and st["aux"] > 0
+    S = torch.empty((n, tn.tn_row_words(n)), dtype=torch.int64, device="cuda")
+    plan.apply(S, init=True)
+    assert plan.status() == 0
+    assert np.array_equal(host_matrix(S, n), oracle.component_matrix(u, v, t, n))
+
+
+@pytest.mark.parametrize("slab,wave", [(64, 5), (26, 7), (64, 152), (16, 3), (128, 2)])
+@pytest.mark.parametrize("window,smem_rows", [(3000, 0), (200, 0)])
+def test_wave_ctas_identical(slab, wave, window, smem_rows):
+    """A matrix spread over a given number of CTAs of two widths (141 row
+    words, stride 144): 64/5 -> 4 x 32 + 1 x 16 words, 26/7 -> 2 x 22 + 5 x 20,
+    64/152 -> 72 x 2 (fewer 16-word units than CTAs), 16/3 -> 9 x 16 (raised
+    to the slab count), 128/2 -> 1 x 80 + 1 x 64 -- through global windows
+    (3,000 events) and shared-memory records (200)."""
+    n = 9000
+    u, v, t = synth.uniform_events(n, 60_000, t_range=20_000, seed=22)
+    du, dv, dt = dev_events(u, v, t)
+    plan = tn.Plan(du, dv, dt, n, window_events=window, slab_words=slab, smem_rows=smem_rows, wave_ctas=wave)
+    S = torch.empty((n, tn.tn_row_words(n)), dtype=torch.int64, device="cuda")
+    plan.apply(S, init=True)
+    assert plan.status() == 0
+    assert np.array_equal(host_matrix(S, n), oracle.component_matrix(u, v, t, n))
+
+
+def test_slab_width_limits():
+    u, v, t = synth.uniform_events(100, 1000, t_range=500, seed=2)
+    du, dv, dt = dev_events(u, v, t)
+    for bad in (130, 129, 17):
+        with pytest.raises(tn.TnError):
+            tn.Plan(du, dv, dt, 100, slab_words=bad)
+    with pytest.raises(tn.TnError):  # a row buffer above 192 KB
+        tn.Plan(du, dv, dt, 100, slab_words=64, smem_rows=385)
+    tn.Plan(du, dv, dt, 100, slab_words=64, smem_rows=384).destroy()
+
+
 def test_carry_across_empty_window():
     """A tie group that spans a nominal window boundary leaves an empty window
     between two local records that share rows."""
