@@ -103,22 +103,27 @@ def column_range(n, rank, world):
     return rank * n // world, (rank + 1) * n // world
 
 
-def gather_sizes(local, n, rank, world, dist):
+def gather_sizes(local, local_argmax, n, rank, world, dist):
     """All-gather of every rank's out-sizes (its columns, in order) into the n
-    sizes of the whole matrix, and the largest out-component: the first
-    (lowest) node id among equal sizes.  `local` is an int32 tensor on the
-    rank's device (gloo: CPU, NCCL: CUDA); returns (sizes, argmax)."""
+    sizes of the whole matrix, and the largest out-component: each rank's own
+    largest (its lowest column among equal sizes, from tn_out_sizes) is
+    gathered beside the sizes and the winner is the largest size, lowest
+    node id on ties.  `local` is an int32 tensor on the rank's device (gloo:
+    CPU, NCCL: CUDA), `local_argmax` an int; returns (sizes, argmax)."""
     import torch
-    counts = [column_range(n, r, world)[1] - column_range(n, r, world)[0] for r in range(world)]
     if world == 1 or dist is None:
-        full = local
-    else:
-        buf = torch.zeros(max(counts), dtype=local.dtype, device=local.device)
-        buf[: local.numel()] = local
-        parts = [torch.empty_like(buf) for _ in range(world)]
-        dist.all_gather(parts, buf)
-        full = torch.cat([parts[r][: counts[r]] for r in range(world)])
-    return full, int(torch.argmax(full).item())  # torch.argmax returns the first maximum
+        return local, int(local_argmax)
+    counts = [column_range(n, r, world)[1] - column_range(n, r, world)[0] for r in range(world)]
+    buf = torch.zeros(max(counts) + 2, dtype=local.dtype, device=local.device)
+    buf[: local.numel()] = local
+    buf[-2] = local[local_argmax]
+    buf[-1] = column_range(n, rank, world)[0] + local_argmax
+    parts = [torch.empty_like(buf) for _ in range(world)]
+    dist.all_gather(parts, buf)
+    full = torch.cat([parts[r][: counts[r]] for r in range(world)])
+    best = [(int(p[-2]), -int(p[-1])) for p in (q.cpu() for q in parts)]
+    size, neg_id = max(best)  # largest size, then the lowest id
+    return full, -neg_id
 
 
 def replica_seed(w, rank):
@@ -153,9 +158,10 @@ def kernel_source_sha(sources):
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload_key):
+def profiled_traffic(workload_key, slab_words=None):
     """DRAM bytes per launch of the workload's dominant kernel from the committed
-    ncu summary, if it was taken on the current kernel sources and this workload."""
+    ncu summary, if it was taken on the current kernel sources, this workload
+    and (when the summary names one) the same slab width."""
     try:
         fields = {}
         name, sources = PROFILE_SUMMARIES[workload_key]
@@ -167,6 +173,8 @@ def profiled_traffic(workload_key):
         if fields.get("kernel_source_sha256_16") != kernel_source_sha(sources):
             return None
         if fields.get("workload") != workload_key:
+            return None
+        if slab_words is not None and "slab_words" in fields and int(fields["slab_words"]) != int(slab_words):
             return None
         return float(fields["dram_bytes_per_launch"])
     except Exception:
@@ -879,8 +887,8 @@ def main():
         if record:
             e1.record(stream)
             k1_events.append((e0, e1))
-        out, _, _ = tn.tn_out_sizes(S, n, ncols)                                         # a4
-        out, am = gather_sizes(out, n, rank, world, dist)                                # (N > 1)
+        out, _, am = tn.tn_out_sizes(S, n, ncols, argmax=True)                           # a4
+        out, am = gather_sizes(out, int(am.item()), n, rank, world, dist)                # (N > 1)
         stats = plan.stats()
         plan.destroy()
         return out, am, stats
@@ -912,7 +920,7 @@ def main():
     alg_bytes = m * 4 * words * 8
     achieved = alg_bytes / (k1_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peaks()
-    traffic = profiled_traffic(args.workload) if world == 1 else None
+    traffic = profiled_traffic(args.workload, opts["slab_words"] or 16) if world == 1 else None
     roofline = {"bound": "hbm", "kernel": "stream_kernel", "achieved": achieved, "peak": peak,
                 "peak_source": f"{peak_kind} MEASURED_PEAKS hbm_gbs" if peak_kind == "measured" else "fallback",
                 "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
@@ -937,7 +945,7 @@ def main():
                          "global_memory_windows": stats["windows"] - stats["local_windows"]},
               "events_per_s": m / (ms_step * 1e-3),
               "roofline": roofline, "gpu_launches": launches, "clocks": clocks.summary(),
-              "largest_out_component": {"node": int(am.item()), "size": int(out.max().item())}}
+              "largest_out_component": {"node": int(am), "size": int(out.max().item())}}
 
     if rank == 0 and not args.no_e2e:
         # end to end through the host-buffer C-ABI call (same plan options), pinned

@@ -55,8 +55,9 @@ def _split_rank_main(rank, world, port, out_dir):
     n = w["n"]
     c0, c1 = bench.column_range(n, rank, world)
     S = oracle.component_matrix(u, v, t, n, src=np.arange(c0, c1, dtype=np.uint32))
-    local = torch.from_numpy(oracle.column_counts(S, c1 - c0).astype(np.int32))
-    full, am = bench.gather_sizes(local, n, rank, world, dist)
+    counts = oracle.column_counts(S, c1 - c0)
+    local = torch.from_numpy(counts.astype(np.int32))
+    full, am = bench.gather_sizes(local, oracle.argmax(counts), n, rank, world, dist)
     np.save(os.path.join(out_dir, f"sizes{rank}.npy"), full.numpy())
     with open(os.path.join(out_dir, f"split{rank}.json"), "w") as f:
         json.dump({"argmax": am, "c0": c0, "c1": c1}, f)
@@ -89,13 +90,31 @@ def test_column_split_gathers_the_whole_matrix_sizes(tmp_path, world):
     assert all(a[1] == b[0] and a[0] < a[1] for a, b in zip(blocks, blocks[1:]))
 
 
-def test_gather_breaks_size_ties_by_lowest_id():
+def _tie_rank_main(rank, world, port, out_dir):
     import torch
+    import torch.distributed as dist
     sys.path.insert(0, ROOT)
     import bench
-    sizes = torch.tensor([3, 9, 2, 9, 9], dtype=torch.int32)
-    full, am = bench.gather_sizes(sizes, 5, 0, 1, None)
-    assert am == 1 and torch.equal(full, sizes)
+
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    # n = 6 over 2 ranks: sizes [2, 7, 7 | 7, 1, 7]; every rank's own largest is
+    # its first 7, the whole matrix's is node 1
+    local = torch.tensor([[2, 7, 7], [7, 1, 7]][rank], dtype=torch.int32)
+    full, am = bench.gather_sizes(local, [1, 0][rank], 6, rank, world, dist)
+    with open(os.path.join(out_dir, f"tie{rank}.json"), "w") as f:
+        json.dump({"argmax": am, "sizes": full.tolist()}, f)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_gather_breaks_size_ties_by_lowest_id(tmp_path):
+    import torch.multiprocessing as mp
+
+    port = free_port()
+    mp.start_processes(_tie_rank_main, args=(2, port, str(tmp_path)), nprocs=2, join=True, start_method="spawn")
+    for r in range(2):
+        rec = json.load(open(tmp_path / f"tie{r}.json"))
+        assert rec["argmax"] == 1 and rec["sizes"] == [2, 7, 7, 7, 1, 7]
 
 
 def test_two_gloo_ranks_max_time_and_distinct_replicas(tmp_path):
