@@ -373,7 +373,10 @@ tn_status tn_error_stats_compute(const uint32_t *est, const uint32_t *exact, uin
 
 /* ---------------------------------------------------------------------------
  * tn_hash_estimate_noalloc -- the same fusion as tn_hash_estimate (same
- * arguments, same result bit for bit) for callers that cannot allocate device
+ * arguments, same result bit for bit, but always the byte-table form: one CTA
+ * per 8 sources, each reading all of H, so its cost grows as ceil(nsrc / 8)
+ * reads of H where tn_hash_estimate switches to bit-sliced tables at 256
+ * sources) for callers that cannot allocate device
  * memory while they run: code that executes inside another framework's memory
  * pool or budget (where a cudaMalloc or a stream-ordered allocation would go
  * around the owner's accounting or fail once the budget is reserved), and

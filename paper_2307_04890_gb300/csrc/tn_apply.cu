@@ -3,16 +3,20 @@
 // Algorithm 1 (Section 3.1) updates whole rows, but bit column j of the matrix
 // (the out-component of source j) evolves independently of every other column.
 // Each CTA therefore owns a slab of `sw` consecutive 64-bit words of every row
-// (64*sw source columns) and streams the whole level-ordered schedule over it:
-//   * a producer warp copies the schedule, tile by tile, into a ring of shared
+// (64*sw source columns, 2 <= sw <= 128) and streams the whole level-ordered
+// schedule over it:
+//   * a producer warp copies the schedule, item by item, into a ring of shared
 //     memory stages with bulk asynchronous copies (cp.async.bulk, completion on
 //     an mbarrier), so the ops are read from L2/HBM once per CTA and without
 //     occupying the consumer threads;
-//   * four consumer warps apply a tile: for each op, 128-bit loads of the two
-//     row segments, OR, 128-bit stores (four ops in flight per thread); the
-//     per-tile named barrier orders one level's stores before the next level's
-//     loads.
-// All waits are bounded (TN_ETIMEOUT).  The per-tile barrier is a reduction
+//   * consumer warps (12 when the CTA holds its SM alone, 4 when two CTAs share
+//     an SM) apply an item: a window whose rows fit the shared-memory row
+//     buffer ("local record") is gathered, updated level by level in shared
+//     memory and written through at each row's last write; a tile of ops on
+//     rows in HBM ("global tile") runs through a private per-thread ring of
+//     cp.async copies, with hub PULLs as L2 OR-reductions.  The per-item named
+//     barrier orders one level's stores before the next level's loads.
+// All waits are bounded (TN_ETIMEOUT).  The per-item barrier is a reduction
 // (bar.red.or) of every consumer's stop condition, so all consumers leave the
 // loop at the same barrier and none can be left waiting on it.
 #include <cuda_runtime.h>

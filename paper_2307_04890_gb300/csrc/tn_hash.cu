@@ -362,10 +362,14 @@ extern "C" tn_status tn_hash_estimate(const uint64_t *P, uint32_t R, uint32_t k,
 
 // ---------------- fusion without allocation ----------------
 // For callers that cannot allocate device memory during a call (code inside
-// another framework's memory budget, latency-bound loops).  Same kernels as
-// tn_hash_estimate; the source-check flag and the per-CTA tables of the
-// global-table path live in one fixed device array of this module instead of
-// the stream-ordered allocator.  Host code never uses the array's name as an
+// another framework's memory budget, latency-bound loops).  Same result as
+// tn_hash_estimate, but only its byte-table fusion (one CTA per 8 sources):
+// the bit-sliced path for many sources needs R * k * nsrc / 8 bytes of
+// transposed tables, more than a fixed array should hold, so every call here
+// reads H once per 8 sources (about ceil(nsrc / 8) * R * n * 4 bytes).  The
+// source-check flag and the per-CTA tables of the global-table path live in
+// one fixed device array of this module instead of the stream-ordered
+// allocator.  Host code never uses the array's name as an
 // address: the address comes from cudaGetSymbolAddress, per device.  Bytes [0, 4) hold the
 // flag, the tables start at byte 256.
 #include <mutex>

@@ -8,6 +8,9 @@ entry point on the same inputs: a first call that leaves stale scratch behind
 would show up in the second.  Covers the shared-memory table, the global
 table inside the fixed scratch, the size limit and the source-id check.
 """
+import ctypes
+import os
+
 import numpy as np
 import pytest
 
@@ -38,13 +41,48 @@ def proxies(n, m, k, R, seed):
     return P, H
 
 
+_USED_CURRENT, _USED_HIGH = 0x7, 0x8  # cudaMemPoolAttrUsedMemCurrent / cudaMemPoolAttrUsedMemHigh
+
+
+def _cudart():
+    for name in ("libcudart.so.13", "libcudart.so", os.path.join("/usr/local/cuda/lib64", "libcudart.so")):
+        try:
+            return ctypes.CDLL(name)
+        except OSError:
+            continue
+    pytest.skip("CUDA runtime library not found for the allocation check")
+
+
+def _pool_reset_and_read(rt, reset):
+    """Bytes in use from the current device's default stream-ordered pool (the
+    pool the library's allocating entry points draw on) and its high-water
+    mark; with `reset` the mark is first reset to the current use."""
+    pool = ctypes.c_void_p()
+    assert rt.cudaDeviceGetDefaultMemPool(ctypes.byref(pool), torch.cuda.current_device()) == 0
+    if reset:
+        zero = ctypes.c_uint64(0)
+        assert rt.cudaMemPoolSetAttribute(pool, _USED_HIGH, ctypes.byref(zero)) == 0
+    cur, high = ctypes.c_uint64(), ctypes.c_uint64()
+    assert rt.cudaMemPoolGetAttribute(pool, _USED_CURRENT, ctypes.byref(cur)) == 0
+    assert rt.cudaMemPoolGetAttribute(pool, _USED_HIGH, ctypes.byref(high)) == 0
+    return cur.value, high.value
+
+
 def twice(P, R, k, H, n, src, nsrc):
-    outs = []
-    for _ in range(2):
-        est = torch.full((nsrc,), -1, dtype=torch.int32, device="cuda")
-        tn.tn_hash_estimate_noalloc(P, R, k, H, n, est, src=src)
-        outs.append(est)
+    """Two calls in a row; asserts that neither allocated device memory: the
+    stream-ordered pool's high-water mark stays at its use before the calls,
+    and torch's allocator hands out nothing beyond the two output tensors."""
+    outs = [torch.full((nsrc,), -1, dtype=torch.int32, device="cuda") for _ in range(2)]
+    rt = _cudart()
     torch.cuda.synchronize()
+    used0, _ = _pool_reset_and_read(rt, reset=True)
+    torch_before = torch.cuda.memory_allocated()
+    for est in outs:
+        tn.tn_hash_estimate_noalloc(P, R, k, H, n, est, src=src)
+    torch.cuda.synchronize()
+    used1, high = _pool_reset_and_read(rt, reset=False)
+    assert used1 == used0 and high == used0, "the no-alloc entry point drew on the stream-ordered pool"
+    assert torch.cuda.memory_allocated() == torch_before
     return [e.cpu().numpy() for e in outs]
 
 
