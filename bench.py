@@ -150,11 +150,20 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+def code_only(text):
+    """C++/CUDA source without comments and blank space: what the compiler sees
+    of it (an edit to a comment does not change the kernel a profile measured)."""
+    import re
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_source_sha(sources):
     h = hashlib.sha256()
     for rel in sources:
-        with open(os.path.join(ROOT, rel), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, rel), encoding="utf-8") as f:
+            h.update(code_only(f.read()).encode())
     return h.hexdigest()[:16]
 
 
