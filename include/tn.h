@@ -243,12 +243,17 @@ tn_status tn_plan_apply(const tn_plan *plan, uint64_t *S, uint32_t ncols,
                         void *stream);
 
 /* One launch over several (plan, matrix) pairs (networks of different n and
- * m, e.g. the R proxies of a hashed network): count entries of each array.
- * Equivalent to calling tn_plan_apply on each pair; all pairs must use
- * distinct S buffers.  Asynchronous, capturable. */
+ * m, e.g. the R proxies of a hashed network, together with the sampled exact
+ * columns of the network they stand for): count entries of each array.
+ * src may be NULL (every matrix has one column per node) or hold count
+ * entries, each NULL or the device source-id list of that matrix's ncols
+ * columns, as in tn_plan_apply (used only with TN_INIT_IDENTITY; ids >= n are
+ * recorded as TN_ERANGE in that plan's status).  Equivalent to calling
+ * tn_plan_apply on each pair; all pairs must use distinct S buffers.
+ * Asynchronous, capturable. */
 tn_status tn_plan_apply_batch(const tn_plan *const *plans, uint64_t *const *S,
-                              const uint32_t *ncols, uint32_t count, uint32_t flags,
-                              void *stream);
+                              const uint32_t *ncols, const uint32_t *const *src,
+                              uint32_t count, uint32_t flags, void *stream);
 
 /* Waits for `stream`, then returns and clears the first error recorded by an
  * asynchronous kernel that used this plan (TN_OK if none). */
@@ -413,18 +418,20 @@ tn_status tn_hash_estimate_noalloc(const uint64_t *P, uint32_t R, uint32_t k, co
  * job's matrix can stay on the device while its event batches arrive).
  *
  * A server runs worker threads on the device that is current when it is
- * created.  tn_server_submit queues a job; the worker admits queued jobs in
- * arrival order whenever fewer than max_active jobs are resident and the
- * job's device memory (matrix + schedules, estimated at submit) fits in
- * memory_budget, so jobs that arrive while others run join the device as soon
- * as a slot and memory free up.  Each admitted job runs on its own stream:
- * its batches are copied in, scheduled and applied in order to one matrix kept
- * on the device (S <- I first; timestamps must not decrease across batches,
- * checked on the device; a batch boundary that falls inside a timestamp group
- * is moved at submit to the end of that group, so the group is applied whole
- * with the following batch, Section 2.1), then its out-sizes (and
- * largest out-component) are copied to the caller's host buffers.  Jobs on
- * different streams overlap on the device.  Results are exactly those of
+ * created.  A job is opened (tn_server_open: n nodes, a bound on the events of
+ * any one of its batches, the host buffers of its results) and then receives
+ * its event batches one at a time (tn_server_push), the last one flagged
+ * TN_LAST_BATCH.  Jobs are admitted in open order whenever fewer than
+ * max_active jobs are resident and the job's device memory (tn_server_job_bytes)
+ * fits in memory_budget, so jobs that arrive while others run join the device
+ * as soon as a slot and memory free up; batches pushed before admission wait
+ * in the job.  An admitted job owns an online state (tn_online_*: S <- I, then
+ * every batch in push order; a timestamp group split by a batch boundary is
+ * held back until the group is complete, Section 2.1) on a stream of its own;
+ * a worker copies each pushed batch in and pushes it to the job's state while
+ * the job's earlier batches and other jobs run on the device.  After the last
+ * batch the out-sizes (and the largest out-component) are copied to the
+ * caller's host buffers.  Results are exactly those of
  * tn_out_component_sizes_host on the concatenated events.
  */
 typedef struct tn_server tn_server;
@@ -435,17 +442,22 @@ typedef struct tn_server_options {
     uint32_t window_events; /* plan options of every batch (0 = defaults) */
     uint32_t slab_words;    /* 0 = per job: the widest even slab (at most 16 words)
                                that still gives the job 16 CTAs, at least 2 words */
-    uint32_t reserved[3];   /* must be zero */
+    uint32_t workers;       /* host worker threads (0 = 8): admission, copies in,
+                               scheduling of batches */
+    uint32_t reserved[2];   /* must be zero */
 } tn_server_options;
 
 typedef struct tn_job_record {
     uint64_t job_id;
-    int32_t status;       /* TN_OK, or the job's error (e.g. TN_EORDER, TN_ERANGE) */
+    int32_t status;           /* TN_OK, or the job's error (e.g. TN_EORDER, TN_ERANGE) */
     uint32_t n;
     uint64_t events;
-    uint64_t t_submit_ns; /* host steady-clock times: submit, admission, results on the host */
-    uint64_t t_admit_ns;
-    uint64_t t_done_ns;
+    uint64_t t_submit_ns;     /* host steady-clock times: open, */
+    uint64_t t_admit_ns;      /* admission, */
+    uint64_t t_done_ns;       /* results on the host, */
+    uint64_t t_last_push_ns;  /* the push of the last batch, */
+    uint64_t t_enqueued_ns;   /* and the end of the host work of the last batch
+                                 (copied in, scheduled, results enqueued) */
 } tn_job_record;
 
 typedef struct tn_server_stats {
@@ -453,15 +465,37 @@ typedef struct tn_server_stats {
     uint64_t bytes_in_use, budget, peak_active, peak_bytes;
 } tn_server_stats;
 
+#define TN_LAST_BATCH 16u     /* tn_server_push: the job's last batch */
+
 tn_status tn_server_create(const tn_server_options *opt, tn_server **server);
 
-/* Queues job `job_id`: n nodes; HOST arrays u, v, t (pinned or pageable) of
- * batch_offsets[nbatches] events, batch b = [batch_offsets[b],
- * batch_offsets[b+1]) (batch_offsets[0] = 0, non-decreasing; a boundary
- * inside a timestamp group moves to the group's end, and each batch must then
- * hold < 2^30 events); out_sizes a HOST uint32[n], argmax a HOST uint32 or NULL.
- * The caller keeps every buffer alive until the job's record is returned by
- * tn_server_poll.  TN_ENOMEM if the job could never fit the budget. */
+/* Device bytes charged to the memory budget for a job of n nodes whose
+ * batches hold at most max_batch_events events: its matrix (rows rounded up
+ * to a multiple of 1,024 as in the online state), sizes, and per batch being
+ * scheduled 160 bytes per event (copy in, held-back group, schedule). */
+uint64_t tn_server_job_bytes(uint32_t n, uint64_t max_batch_events);
+
+/* Opens job `job_id` (unique among the server's open jobs): n nodes, batches of
+ * at most max_batch_events events, out_sizes a HOST uint32[n], argmax a HOST
+ * uint32 or NULL (both written when the job finishes).  TN_ENOMEM if the job
+ * could never fit the budget, TN_EINVAL for a bad argument or a job id that
+ * is already open. */
+tn_status tn_server_open(tn_server *server, uint64_t job_id, uint32_t n, uint64_t max_batch_events,
+                         uint32_t *out_sizes, uint32_t *argmax);
+
+/* Appends a batch to an open job: HOST arrays u, v (uint32, < n) and t (int64,
+ * non-decreasing, continuing the job's earlier batches; equal timestamps may
+ * span a boundary) of m <= max_batch_events events, pinned or pageable, kept
+ * alive by the caller until the job's record is returned by tn_server_poll.
+ * flags: 0 or TN_LAST_BATCH (no further batches: the job's results follow).
+ * A batch out of order or out of range ends the job with TN_EORDER /
+ * TN_ERANGE in its record.  TN_EINVAL for an unknown or closed job. */
+tn_status tn_server_push(tn_server *server, uint64_t job_id, const uint32_t *u, const uint32_t *v,
+                         const int64_t *t, uint64_t m, uint32_t flags);
+
+/* Open + one push per batch: HOST arrays u, v, t of batch_offsets[nbatches]
+ * events, batch b = [batch_offsets[b], batch_offsets[b+1]) (batch_offsets[0] =
+ * 0, non-decreasing, each batch < 2^30 events). */
 tn_status tn_server_submit(tn_server *server, uint64_t job_id, uint32_t n, const uint32_t *u,
                            const uint32_t *v, const int64_t *t, const uint64_t *batch_offsets,
                            uint32_t nbatches, uint32_t *out_sizes, uint32_t *argmax);
@@ -473,8 +507,10 @@ tn_status tn_server_poll(tn_server *server, tn_job_record *records, uint32_t cap
 
 tn_status tn_server_get_stats(tn_server *server, tn_server_stats *stats);
 
-/* Finishes every queued and running job, then stops the worker and frees the
- * server (records not yet polled are dropped). */
+/* Finishes every admitted and queued job whose last batch was pushed (a job
+ * that never receives its last batch is dropped with its pending batches),
+ * then stops the workers and frees the server (records not yet polled are
+ * dropped). */
 tn_status tn_server_destroy(tn_server *server);
 
 /* ---------------------------------------------------------------------------

@@ -26,7 +26,7 @@ __all__ = [
     "Plan", "tn_plan_apply_batch", "Server", "BatchGraph", "tn_autotune", "tn_selftest_wait_timeout",
     "tn_hll_sketches", "tn_hll_estimate", "tn_grow_matrix", "Online",
     "TN_OK", "TN_EINVAL", "TN_ERANGE", "TN_EORDER", "TN_ENOMEM", "TN_ECUDA", "TN_ETIMEOUT", "TN_ESCRATCH",
-    "TN_INIT_IDENTITY", "TN_REVERSE", "TN_DIRECTED", "TN_GROUP_END",
+    "TN_INIT_IDENTITY", "TN_REVERSE", "TN_DIRECTED", "TN_GROUP_END", "TN_LAST_BATCH", "tn_server_job_bytes",
 ]
 
 TN_OK, TN_EINVAL, TN_ERANGE, TN_EORDER, TN_ENOMEM, TN_ECUDA, TN_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
@@ -35,6 +35,7 @@ TN_INIT_IDENTITY = 1
 TN_REVERSE = 2
 TN_DIRECTED = 4
 TN_GROUP_END = 8
+TN_LAST_BATCH = 16
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIBRARY_PATH = os.path.join(_HERE, "libtn.so")
@@ -69,13 +70,14 @@ class _ErrorStats(ctypes.Structure):
 class _ServerOptions(ctypes.Structure):
     _fields_ = [("memory_budget", ctypes.c_uint64), ("max_active", ctypes.c_uint32),
                 ("window_events", ctypes.c_uint32), ("slab_words", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 3)]
+                ("workers", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 2)]
 
 
 class _JobRecord(ctypes.Structure):
     _fields_ = [("job_id", ctypes.c_uint64), ("status", ctypes.c_int32), ("n", ctypes.c_uint32),
                 ("events", ctypes.c_uint64), ("t_submit_ns", ctypes.c_uint64), ("t_admit_ns", ctypes.c_uint64),
-                ("t_done_ns", ctypes.c_uint64)]
+                ("t_done_ns", ctypes.c_uint64), ("t_last_push_ns", ctypes.c_uint64),
+                ("t_enqueued_ns", ctypes.c_uint64)]
 
 
 class _ServerStats(ctypes.Structure):
@@ -117,7 +119,7 @@ def load_library(path: str | None = None):
         "tn_out_sizes": ([vp, u32, u32, vp, vp, vp, vp], i32),
         "tn_plan_create": ([vp, vp, vp, u64, u32, vp, vp, vp, ctypes.POINTER(vp)], i32),
         "tn_plan_apply": ([vp, vp, u32, vp, vp, u32, vp], i32),
-        "tn_plan_apply_batch": ([vp, vp, vp, u32, u32, vp], i32),
+        "tn_plan_apply_batch": ([vp, vp, vp, vp, u32, u32, vp], i32),
         "tn_plan_status": ([vp, vp], i32),
         "tn_plan_get_stats": ([vp, ctypes.POINTER(_Stats)], i32),
         "tn_plan_destroy": ([vp, vp], i32),
@@ -135,6 +137,9 @@ def load_library(path: str | None = None):
         "tn_hll_estimate": ([vp, u32, u32, vp, vp], i32),
         "tn_server_create": ([ctypes.POINTER(_ServerOptions), ctypes.POINTER(vp)], i32),
         "tn_server_submit": ([vp, u64, u32, vp, vp, vp, vp, u32, vp, vp], i32),
+        "tn_server_open": ([vp, u64, u32, u64, vp, vp], i32),
+        "tn_server_push": ([vp, u64, vp, vp, vp, u64, u32], i32),
+        "tn_server_job_bytes": ([u32, u64], u64),
         "tn_server_poll": ([vp, ctypes.POINTER(_JobRecord), u32, ctypes.POINTER(u32), u32], i32),
         "tn_server_get_stats": ([vp, ctypes.POINTER(_ServerStats)], i32),
         "tn_server_destroy": ([vp], i32),
@@ -425,30 +430,46 @@ class Plan:
             pass
 
 
-def tn_plan_apply_batch(plans, mats, ncols=None, init: bool = True, stream=None):
-    """One launch over several (plan, matrix) pairs."""
+def tn_plan_apply_batch(plans, mats, ncols=None, init: bool = True, srcs=None, stream=None):
+    """One launch over several (plan, matrix) pairs; ``srcs``: None, or one
+    entry per pair (None = all nodes, else a device int32 tensor of the
+    matrix's source ids, used with ``init``)."""
     lib = load_library()
     count = len(plans)
     ncols = ncols or [p.n for p in plans]
     hp = (ctypes.c_void_p * count)(*[p.handle for p in plans])
     hs = (ctypes.c_void_p * count)(*[m.data_ptr() for m in mats])
     hn = (ctypes.c_uint32 * count)(*ncols)
-    _check(lib.tn_plan_apply_batch(hp, hs, hn, count, TN_INIT_IDENTITY if init else 0, _stream(stream)),
+    hsrc = None
+    if srcs is not None:
+        for s_ in srcs:
+            if s_ is not None:
+                _dev(s_, ("int32", "uint32"), "srcs")
+        hsrc = (ctypes.c_void_p * count)(*[None if s_ is None else s_.data_ptr() for s_ in srcs])
+    _check(lib.tn_plan_apply_batch(hp, hs, hn, hsrc, count, TN_INIT_IDENTITY if init else 0, _stream(stream)),
            "tn_plan_apply_batch")
     return mats
+
+
+def tn_server_job_bytes(n: int, max_batch_events: int) -> int:
+    """Device bytes a serving job of n nodes and batches of at most
+    ``max_batch_events`` events is charged against the server's budget."""
+    return int(load_library().tn_server_job_bytes(n, max_batch_events))
 
 
 class Server:
     """Continuous admission of component-matrix jobs (tn_server_*).
 
-    ``submit`` takes host numpy arrays and keeps them (and the result buffer)
-    alive until the job's record comes back from ``poll``; ``results[job_id]``
-    then holds ``(out_sizes, argmax)``.
+    ``submit`` (all batches at once) or ``open`` + ``push`` (batches as they
+    arrive) take host numpy arrays and keep them (and the result buffer)
+    alive until the job's record comes back from ``poll``;
+    ``results[job_id]`` then holds ``(out_sizes, argmax)``.
     """
 
-    def __init__(self, memory_budget: int = 0, max_active: int = 0, window_events: int = 0, slab_words: int = 0):
+    def __init__(self, memory_budget: int = 0, max_active: int = 0, window_events: int = 0, slab_words: int = 0,
+                 workers: int = 0):
         lib = load_library()
-        opt = _ServerOptions(memory_budget, max_active, window_events, slab_words)
+        opt = _ServerOptions(memory_budget, max_active, window_events, slab_words, workers)
         h = ctypes.c_void_p()
         _check(lib.tn_server_create(ctypes.byref(opt), ctypes.byref(h)), "tn_server_create")
         self._h = h
@@ -466,10 +487,33 @@ class Server:
             raise ValueError("batch offsets must end at the number of events")
         out = np.zeros(n, dtype=np.uint32)
         am = np.zeros(1, dtype=np.uint32)
-        self._keep[job_id] = (u, v, t, offs, out, am)
+        self._keep[job_id] = [out, am, (u, v, t, offs)]
         _check(lib.tn_server_submit(self._h, job_id, n, u.ctypes.data, v.ctypes.data, t.ctypes.data,
                                     offs.ctypes.data, len(offs) - 1, out.ctypes.data, am.ctypes.data),
                "tn_server_submit")
+
+    def open(self, job_id: int, n: int, max_batch_events: int):
+        """Opens a job whose batches (at most ``max_batch_events`` events each)
+        follow with ``push``."""
+        import numpy as np
+        out = np.zeros(n, dtype=np.uint32)
+        am = np.zeros(1, dtype=np.uint32)
+        self._keep[job_id] = [out, am]
+        _check(load_library().tn_server_open(self._h, job_id, n, max_batch_events, out.ctypes.data, am.ctypes.data),
+               "tn_server_open")
+
+    def push(self, job_id: int, u, v, t, last: bool = False):
+        """Appends a batch of host events to an open job (``last``: the job's
+        final batch, after which its results follow)."""
+        import numpy as np
+        u = np.ascontiguousarray(u, dtype=np.uint32)
+        v = np.ascontiguousarray(v, dtype=np.uint32)
+        t = np.ascontiguousarray(t, dtype=np.int64)
+        if len(v) != len(u) or len(t) != len(u):
+            raise ValueError("u, v and t must have the same length")
+        self._keep.setdefault(job_id, [None, None]).append((u, v, t))
+        _check(load_library().tn_server_push(self._h, job_id, u.ctypes.data, v.ctypes.data, t.ctypes.data, len(u),
+                                             TN_LAST_BATCH if last else 0), "tn_server_push")
 
     def poll(self, wait_ms: int = 0, capacity: int = 256):
         """Records of finished jobs: dicts with job_id, status, n, events and
@@ -483,7 +527,7 @@ class Server:
             d = {name: getattr(r, name) for name, _ in _JobRecord._fields_}
             kept = self._keep.pop(d["job_id"], None)
             if kept is not None:
-                self.results[d["job_id"]] = (kept[4], int(kept[5][0]))
+                self.results[d["job_id"]] = (kept[0], int(kept[1][0]))
             out.append(d)
         return out
 

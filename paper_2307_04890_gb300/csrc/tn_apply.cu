@@ -767,13 +767,14 @@ extern "C" tn_status tn_plan_apply(const tn_plan *plan, uint64_t *S, uint32_t nc
 }
 
 extern "C" tn_status tn_plan_apply_batch(const tn_plan *const *plans, uint64_t *const *S, const uint32_t *ncols,
-                                         uint32_t count, uint32_t flags, void *stream)
+                                         const uint32_t *const *src, uint32_t count, uint32_t flags, void *stream)
 {
     if (!plans || !S || !ncols || count == 0 || (flags & ~TN_INIT_IDENTITY)) return TN_EINVAL;
-    const uint32_t **src = (const uint32_t **)calloc(count, sizeof(uint32_t *));
-    if (!src) return TN_ENOMEM;
-    tn_status rc = apply_jobs(plans, S, ncols, src, nullptr, count, flags, (cudaStream_t)stream);
-    free(src);
+    if (src) return apply_jobs(plans, S, ncols, src, nullptr, count, flags, (cudaStream_t)stream);
+    const uint32_t **none = (const uint32_t **)calloc(count, sizeof(uint32_t *));
+    if (!none) return TN_ENOMEM;
+    tn_status rc = apply_jobs(plans, S, ncols, none, nullptr, count, flags, (cudaStream_t)stream);
+    free(none);
     return rc;
 }
 

@@ -124,7 +124,7 @@ tn_status time_apply(tn_plan *plan, uint64_t *const *mats, uint32_t count, uint3
         std::vector<const tn_plan *> plans(count, plan);
         std::vector<uint32_t> nc(count, ncols);
         if (rc == TN_OK)
-            rc = tn_plan_apply_batch(plans.data(), mats, nc.data(), count, src ? 0u : TN_INIT_IDENTITY, st);
+            rc = tn_plan_apply_batch(plans.data(), mats, nc.data(), nullptr, count, src ? 0u : TN_INIT_IDENTITY, st);
         cudaEventRecord(e1, st);
         if (cudaEventSynchronize(e1) != cudaSuccess) rc = TN_ECUDA;
         float t = 0.f;

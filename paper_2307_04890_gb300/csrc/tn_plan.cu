@@ -188,6 +188,128 @@ __device__ inline uint32_t hlookup(const uint32_t *hkey, const uint32_t *hval, u
     return hval[s];
 }
 
+// Timestamp groups of at least this many events are scheduled by the whole CTA.
+constexpr uint32_t kParGroup = 128;
+constexpr uint32_t kClaim = 0xFFFFFFFEu;  // run / temp slot being assigned
+
+// Scan state shared by the threads of a window's CTA: nruns, naux, ntemp,
+// maxlev, next event, end of the large group at it.
+enum { kScRuns = 0, kScAux, kScTemp, kScMaxlev, kScNext, kScEnd, kScCount };
+
+// The snapshot rule for one large undirected timestamp group [i, g1), with
+// every thread of the CTA.  It yields the same roles, levels, runs (PULLs),
+// saved-row slots and source lists as the sequential scan; only the numbering
+// of runs and slots and the order of ops inside a level and of sources inside
+// a PULL list may differ, and none of them changes the result.  Nodes that
+// occur once in the group take part in exactly one event, so a lone event
+// (both ends once) touches no other event's rows and gets its level at once;
+// the other events share one level L = 1 + the latest level of their nodes,
+// with the PULLs at L + 1.  Phases are separated by barriers, so a run's
+// and a slot's number are final before anyone reads them.
+__device__ void schedule_group_parallel(uint32_t i, uint32_t g1, const uint32_t *lu, const uint32_t *lv,
+                                        uint32_t *grp, uint32_t *evl, uint32_t *run_node, uint32_t *run_aux,
+                                        uint32_t *run_lev, uint32_t *run_temp, uint32_t *nlev, uint32_t *ncnt,
+                                        uint32_t *nrun, uint32_t *auxw, uint32_t *sc)
+{
+    __shared__ uint32_t Lc, any, run0;
+    const uint32_t T = blockDim.x, tid = threadIdx.x;
+    for (uint32_t j = i + tid; j < g1; j += T) {
+        ncnt[lu[j]] = 0;
+        ncnt[lv[j]] = 0;
+        nrun[lu[j]] = kNone;
+        nrun[lv[j]] = kNone;
+    }
+    if (tid == 0) {
+        Lc = 0;
+        any = 0;
+        run0 = sc[kScRuns];
+    }
+    __syncthreads();
+    for (uint32_t j = i + tid; j < g1; j += T)
+        if (lu[j] != lv[j]) {
+            atomicAdd(&ncnt[lu[j]], 1u);
+            atomicAdd(&ncnt[lv[j]], 1u);
+        }
+    __syncthreads();
+    // roles; lone events' levels; one run (PULL) per node occurring several times
+    auto claim_run = [&](uint32_t x) {
+        if (atomicCAS(&nrun[x], kNone, kClaim) != kNone) return;
+        const uint32_t r = atomicAdd(&sc[kScRuns], 1u);
+        const uint32_t b = atomicAdd(&sc[kScAux], 1u + ncnt[x]);
+        run_node[r] = x;
+        run_aux[r] = b;
+        run_lev[r] = 0;  // fill counter until the level is known
+        run_temp[r] = kNone;
+        auxw[b] = ncnt[x];
+        nrun[x] = r;
+    };
+    for (uint32_t j = i + tid; j < g1; j += T) {
+        const uint32_t x = lu[j], y = lv[j];
+        if (x == y) {
+            grp[j] = kFlagNoop;
+            continue;
+        }
+        const bool sx = ncnt[x] > 1, sy = ncnt[y] > 1;
+        if (!sx && !sy) {
+            const uint32_t L = 1 + max(nlev[x], nlev[y]);
+            nlev[x] = L;
+            nlev[y] = L;
+            evl[j] = L;
+            grp[j] = kFlagIso;
+            atomicMax(&sc[kScMaxlev], L);
+            continue;
+        }
+        atomicMax(&Lc, max(nlev[x], nlev[y]));
+        any = 1;
+        grp[j] = (sx ? kFlagShA : 0u) | (sy ? kFlagShB : 0u);
+        if (sx) claim_run(x);
+        if (sy) claim_run(y);
+    }
+    __syncthreads();
+    // saved rows: a node occurring several times whose partner does too is
+    // read from a copy of its old row
+    auto claim_temp = [&](uint32_t r) {
+        if (atomicCAS(&run_temp[r], kNone, kClaim) == kNone) run_temp[r] = atomicAdd(&sc[kScTemp], 1u);
+    };
+    for (uint32_t j = i + tid; j < g1; j += T)
+        if (grp[j] == (kFlagShA | kFlagShB)) {
+            claim_temp(nrun[lu[j]]);
+            claim_temp(nrun[lv[j]]);
+        }
+    __syncthreads();
+    // source lists
+    for (uint32_t j = i + tid; j < g1; j += T) {
+        const uint32_t f = grp[j];
+        if (f & (kFlagNoop | kFlagIso)) continue;
+        const uint32_t x = lu[j], y = lv[j];
+        if (f == (kFlagShA | kFlagShB)) {
+            const uint32_t rx = nrun[x], ry = nrun[y];
+            auxw[run_aux[rx] + 1 + atomicAdd(&run_lev[rx], 1u)] = kTempRef | run_temp[ry];
+            auxw[run_aux[ry] + 1 + atomicAdd(&run_lev[ry], 1u)] = kTempRef | run_temp[rx];
+        } else if (f & kFlagShA) {
+            const uint32_t rx = nrun[x];
+            auxw[run_aux[rx] + 1 + atomicAdd(&run_lev[rx], 1u)] = y;
+        } else {
+            const uint32_t ry = nrun[y];
+            auxw[run_aux[ry] + 1 + atomicAdd(&run_lev[ry], 1u)] = x;
+        }
+    }
+    __syncthreads();
+    // levels of the shared part: ONEWAY / COPY at L, PULL at L + 1
+    if (any) {
+        const uint32_t L = Lc + 1;
+        for (uint32_t j = i + tid; j < g1; j += T) {
+            if (grp[j] & (kFlagNoop | kFlagIso)) continue;
+            evl[j] = L;
+            nlev[lu[j]] = L + 1;
+            nlev[lv[j]] = L + 1;
+        }
+        for (uint32_t r = run0 + tid; r < sc[kScRuns]; r += T) run_lev[r] = L;
+        if (tid == 0) atomicMax(&sc[kScMaxlev], L + 1);
+    }
+    __syncthreads();
+}
+
 __device__ void schedule_window(const PlanArgs &a, uint32_t w, uint32_t *arena)
 {
     __shared__ uint32_t warp_sums[32];
@@ -242,12 +364,18 @@ __device__ void schedule_window(const PlanArgs &a, uint32_t w, uint32_t *arena)
     }
     __syncthreads();
 
-    // 2. sequential level scan (one thread), in time order.  Rows are named by
-    //    local ids here; PULL source lists hold local ids or temp references.
+    // 2. level scan in time order: one thread takes the groups one by one and
+    //    hands every large undirected group to the whole CTA.  Rows are named
+    //    by local ids here; PULL source lists hold local ids or temp references.
+    __shared__ uint32_t sc[kScCount];
+    if (tid == 0)
+        for (int q = 0; q < kScCount; ++q) sc[q] = 0;
+    __syncthreads();
+    for (;;) {
     if (tid == 0) {
-        uint32_t nruns = 0, naux = 0, ntemp = 0, maxlev = 0;
+        uint32_t nruns = sc[kScRuns], naux = sc[kScAux], ntemp = sc[kScTemp], maxlev = sc[kScMaxlev];
         uint32_t *auxw = a.aux_stage + 3 * s;
-        uint32_t i = 0;
+        uint32_t i = sc[kScNext];
         while (i < E && a.directed) {
             // directed events x -> y: only y is written.  A lone event is one
             // ONEWAY y |= x; a tie group becomes one PULL per receiver (level
@@ -327,6 +455,7 @@ __device__ void schedule_window(const PlanArgs &a, uint32_t w, uint32_t *arena)
         }
         while (i < E) {
             const uint32_t g = grp[i];
+            if (i + kParGroup <= E && grp[i + kParGroup - 1] == g) break;  // a large group: the whole CTA
             uint32_t g1 = i + 1;
             while (g1 < E && grp[g1] == g) ++g1;
             if (g1 == i + 1) {
@@ -429,10 +558,33 @@ __device__ void schedule_window(const PlanArgs &a, uint32_t w, uint32_t *arena)
             }
             i = g1;
         }
-        res[1] = maxlev;
-        res[2] = naux;
-        res[3] = ntemp;
-        res[4] = nruns;
+        sc[kScRuns] = nruns;
+        sc[kScAux] = naux;
+        sc[kScTemp] = ntemp;
+        sc[kScMaxlev] = maxlev;
+        sc[kScNext] = i;
+        if (i < E) {  // end of the large group at i: first index past it (grp is non-decreasing there)
+            uint32_t lo = i, hi = E;
+            while (lo < hi) {
+                const uint32_t mid = lo + (hi - lo) / 2;
+                if (grp[mid] > grp[i]) hi = mid;
+                else lo = mid + 1;
+            }
+            sc[kScEnd] = lo;
+        }
+    }
+    __syncthreads();
+    if (sc[kScNext] >= E) break;
+    schedule_group_parallel(sc[kScNext], sc[kScEnd], lu, lv, grp, evl, run_node, run_aux, run_lev, run_temp, nlev,
+                            ncnt, nrun, a.aux_stage + 3 * s, sc);
+    if (tid == 0) sc[kScNext] = sc[kScEnd];
+    __syncthreads();
+    }
+    if (tid == 0) {
+        res[1] = sc[kScMaxlev];
+        res[2] = sc[kScAux];
+        res[3] = sc[kScTemp];
+        res[4] = sc[kScRuns];
         res[6] = 0;
     }
     __syncthreads();

@@ -1,39 +1,44 @@
-// Serving engine: continuous admission of component-matrix jobs.
+// Serving engine: continuous admission of component-matrix jobs whose event
+// batches arrive over time.
 //
-// The paper's method is a streaming algorithm (Section 3.5): new events are
-// applied to the stored component matrix with the same rule, so a job's state
-// (its matrix S) can live on the device across incremental event batches.
-// This engine serves many such jobs at once:
-//   * submit() queues a job (n nodes, its events split into batches of
-//     increasing time) together with the host buffer its out-sizes go to;
-//   * a worker thread admits queued jobs in arrival order whenever a slot is
-//     free and the job's device memory fits the budget, so jobs that arrive
-//     while others run join the device as soon as memory frees up;
-//   * an admitted job gets its own stream: its events are copied in, every
-//     batch is scheduled (tn_plan_create), and the batches are applied in
-//     order to the same S with the t_last order gate, followed by the
-//     out-sizes and the copy back.  Jobs on different streams overlap on the
-//     device.  A batch boundary inside a timestamp group is moved to the end
-//     of the group at submit, so each group is applied whole;
-//   * finished jobs release their memory and report timings through poll().
+// The paper's method is one pass over a time-ordered stream (Section 3.5), so
+// a job's state -- its component matrix -- can stay on the device while its
+// event batches arrive.  This engine serves many such jobs at once:
+//   * tn_server_open registers a job (n nodes, a bound on its batch size, the
+//     host buffers of its results) and queues it for admission;
+//   * tn_server_push hands the job a batch of host events; batches wait in the
+//     job until it is admitted and are applied in push order;
+//   * worker threads admit queued jobs in open order whenever a slot is free
+//     and the job's device memory fits the budget.  An admitted job owns an
+//     online state (tn_online_*: S <- I, then each batch; a timestamp group
+//     split by a batch boundary is held back until it is complete) on a
+//     stream of its own.  A worker copies a pending batch in and pushes it to
+//     the job's state; one worker at a time serves a given job, so its batches
+//     keep their order while the other workers serve other jobs;
+//   * after the batch marked last, the out-sizes are computed and copied back
+//     on the job's stream; a finished job releases its memory and reports its
+//     timings through poll().
+// Jobs on different streams overlap on the device.  tn_server_submit is
+// open + one push per batch.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
 
-#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
 #include <mutex>
 #include <new>
 #include <thread>
+#include <unordered_map>
 #include <vector>
 
 #include "tn_internal.cuh"
 
 namespace {
 
-constexpr int kServeWorkers = 4;
+constexpr uint32_t kDefaultWorkers = 8;
+constexpr uint64_t kBytesPerBatchEvent = 160;  // copy in 16, held-back group 16, schedule ~128
 
 uint64_t now_ns()
 {
@@ -42,23 +47,33 @@ uint64_t now_ns()
         .count();
 }
 
+struct ServeBatch {
+    const uint32_t *u = nullptr, *v = nullptr;
+    const int64_t *t = nullptr;
+    uint64_t m = 0;
+    bool last = false;
+};
+
 struct ServeJob {
     uint64_t id = 0;
     uint32_t n = 0;
-    const uint32_t *hu = nullptr, *hv = nullptr;
-    const int64_t *ht = nullptr;
-    std::vector<uint64_t> offs;  // batch b = events [offs[b], offs[b+1])
+    uint64_t max_batch = 0;
     uint32_t *h_out = nullptr, *h_argmax = nullptr;
     uint64_t bytes = 0;  // device bytes charged to the budget
-    // device state
+    // guarded by the server's mutex
+    std::deque<ServeBatch> batches;  // pushed, not yet applied
+    bool closed = false;             // the last batch has been pushed
+    bool busy = false;               // a worker is serving one of its batches
+    bool finishing = false;          // results enqueued (or the job failed): retire when done
+    uint64_t events = 0;
+    // device state, used by one worker at a time
     cudaStream_t st = nullptr;
     cudaEvent_t done = nullptr;
-    uint64_t *S = nullptr;
-    int64_t *t_last = nullptr;
-    uint32_t *d_out = nullptr, *d_am = nullptr;
-    std::vector<tn_plan *> plans;
+    tn_online *on = nullptr;
+    uint32_t *du = nullptr, *dv = nullptr, *d_out = nullptr, *d_am = nullptr;
+    int64_t *dt = nullptr;
     tn_status status = TN_OK;
-    uint64_t t_submit = 0, t_admit = 0, t_done = 0;
+    uint64_t t_open = 0, t_admit = 0, t_last_push = 0, t_enqueued = 0, t_done = 0;
 };
 
 }  // namespace
@@ -69,38 +84,19 @@ struct tn_server {
     uint64_t budget = 0;
     std::mutex mu;
     std::condition_variable cv;
-    std::deque<ServeJob *> queue;
-    std::vector<ServeJob *> active;
+    std::unordered_map<uint64_t, ServeJob *> open;  // opened, not yet retired
+    std::deque<ServeJob *> queue;                   // waiting for admission, in open order
+    std::vector<ServeJob *> active;                 // admitted
     std::deque<tn_job_record> finished;
     std::condition_variable finished_cv;
     uint64_t in_use = 0;
     uint64_t admitted = 0, completed = 0, peak_active = 0, peak_bytes = 0;
-    uint64_t starting = 0;  // jobs admitted whose start is in progress
+    uint64_t starting = 0;  // admissions in progress
     bool stop = false;
     std::vector<std::thread> workers;
 };
 
 namespace {
-
-uint64_t job_bytes(uint32_t n, uint64_t m, uint64_t max_batch)
-{
-    // matrix + sizes + t_last, the largest batch's events while its plan is
-    // built, and the schedules (about 16 bytes per event, 64 while building)
-    return (uint64_t)n * tn_row_words(n) * 8 + (uint64_t)n * 4 + 64 + max_batch * 16 + m * 16 + max_batch * 64;
-}
-
-void release_job(ServeJob *j)
-{
-    for (tn_plan *p : j->plans)
-        if (p) tn_plan_destroy(p, j->st);
-    if (j->S) cudaFreeAsync(j->S, j->st);
-    if (j->t_last) cudaFreeAsync(j->t_last, j->st);
-    if (j->d_out) cudaFreeAsync(j->d_out, j->st);
-    if (j->d_am) cudaFreeAsync(j->d_am, j->st);
-    if (j->st) cudaStreamSynchronize(j->st);
-    if (j->done) cudaEventDestroy(j->done);
-    if (j->st) cudaStreamDestroy(j->st);
-}
 
 #define SERVE_TRY(expr)                           \
     do {                                          \
@@ -123,96 +119,74 @@ uint32_t serve_slab_words(uint32_t n)
     return sw < 2 ? 2u : (uint32_t)sw;
 }
 
-// Copies the job in, schedules every batch and enqueues the whole job on its
-// stream.  Runs on the worker thread.
+// Stream, online state, copy-in buffers and result buffers of an admitted job.
 tn_status start_job(tn_server *s, ServeJob *j)
 {
     SERVE_TRY(cudaStreamCreateWithFlags(&j->st, cudaStreamNonBlocking));
     SERVE_TRY(cudaEventCreateWithFlags(&j->done, cudaEventDisableTiming));
-    const uint64_t ld = tn_row_words(j->n);
-    const uint32_t nb = (uint32_t)j->offs.size() - 1;
-    SERVE_TRY(cudaMallocAsync((void **)&j->S, (uint64_t)j->n * ld * 8, j->st));
-    SERVE_TRY(cudaMallocAsync((void **)&j->t_last, sizeof(int64_t), j->st));
+    const uint64_t mb = j->max_batch ? j->max_batch : 1;
+    SERVE_TRY(cudaMallocAsync((void **)&j->du, mb * 4, j->st));
+    SERVE_TRY(cudaMallocAsync((void **)&j->dv, mb * 4, j->st));
+    SERVE_TRY(cudaMallocAsync((void **)&j->dt, mb * 8, j->st));
     SERVE_TRY(cudaMallocAsync((void **)&j->d_out, (uint64_t)j->n * 4, j->st));
     SERVE_TRY(cudaMallocAsync((void **)&j->d_am, 4, j->st));
-    // schedules of all batches (they depend on the events only)
-    uint64_t max_batch = 0;
-    for (uint32_t b = 0; b < nb; ++b)
-        if (j->offs[b + 1] - j->offs[b] > max_batch) max_batch = j->offs[b + 1] - j->offs[b];
-    uint32_t *du = nullptr, *dv = nullptr;
-    int64_t *dt = nullptr;
-    if (max_batch) {
-        SERVE_TRY(cudaMallocAsync((void **)&du, max_batch * 4, j->st));
-        SERVE_TRY(cudaMallocAsync((void **)&dv, max_batch * 4, j->st));
-        SERVE_TRY(cudaMallocAsync((void **)&dt, max_batch * 8, j->st));
-    }
     tn_plan_options opt;
     memset(&opt, 0, sizeof(opt));
     opt.window_events = s->opt.window_events;
     opt.slab_words = s->opt.slab_words ? s->opt.slab_words : serve_slab_words(j->n);
-    tn_status rc = TN_OK;
-    for (uint32_t b = 0; b < nb && rc == TN_OK; ++b) {
-        const uint64_t e0 = j->offs[b], mb = j->offs[b + 1] - e0;
-        if (mb == 0) {
-            j->plans.push_back(nullptr);
-            continue;
-        }
-        cudaError_t err = cudaMemcpyAsync(du, j->hu + e0, mb * 4, cudaMemcpyHostToDevice, j->st);
-        if (err == cudaSuccess) err = cudaMemcpyAsync(dv, j->hv + e0, mb * 4, cudaMemcpyHostToDevice, j->st);
-        if (err == cudaSuccess) err = cudaMemcpyAsync(dt, j->ht + e0, mb * 8, cudaMemcpyHostToDevice, j->st);
-        if (err != cudaSuccess) {
-            tn_internal_set_cuda_error(err);
-            rc = TN_ECUDA;
-            break;
-        }
-        tn_plan *p = nullptr;
-        rc = tn_plan_create(du, dv, dt, mb, j->n, nullptr, &opt, j->st, &p);
-        j->plans.push_back(p);
+    return tn_online_create(j->n, &opt, j->st, &j->on);
+}
+
+// One batch of an admitted job: copy in, push to the online state, and after
+// the last batch the out-sizes and their copy to the caller.
+tn_status serve_batch(ServeJob *j, const ServeBatch &b)
+{
+    if (b.m) {
+        SERVE_TRY(cudaMemcpyAsync(j->du, b.u, b.m * 4, cudaMemcpyHostToDevice, j->st));
+        SERVE_TRY(cudaMemcpyAsync(j->dv, b.v, b.m * 4, cudaMemcpyHostToDevice, j->st));
+        SERVE_TRY(cudaMemcpyAsync(j->dt, b.t, b.m * 8, cudaMemcpyHostToDevice, j->st));
     }
-    if (du) cudaFreeAsync(du, j->st);
-    if (dv) cudaFreeAsync(dv, j->st);
-    if (dt) cudaFreeAsync(dt, j->st);
+    tn_status rc = tn_online_push(j->on, j->du, j->dv, j->dt, b.m, b.last ? TN_GROUP_END : 0u, j->st);
+    if (rc != TN_OK || !b.last) return rc;
+    tn_online_state state;
+    rc = tn_online_get_state(j->on, &state);
     if (rc != TN_OK) return rc;
-    // S <- I, then the batches in order; t_last orders them on the device
-    const int64_t lowest = INT64_MIN;
-    SERVE_TRY(cudaMemcpyAsync(j->t_last, &lowest, sizeof(lowest), cudaMemcpyHostToDevice, j->st));
-    bool first = true;
-    for (tn_plan *p : j->plans) {
-        if (!p) continue;
-        rc = tn_plan_apply(p, j->S, j->n, nullptr, j->t_last, first ? TN_INIT_IDENTITY : 0u, j->st);
-        if (rc != TN_OK) return rc;
-        first = false;
-    }
-    if (first) {  // no events at all: the identity
-        rc = tn_init_matrix(j->S, j->n, j->n, nullptr, j->st);
-        if (rc != TN_OK) return rc;
-    }
-    rc = tn_out_sizes(j->S, j->n, j->n, j->d_out, nullptr, j->d_am, j->st);
+    rc = tn_out_sizes(state.S, j->n, j->n, j->d_out, nullptr, j->d_am, j->st);
     if (rc != TN_OK) return rc;
     SERVE_TRY(cudaMemcpyAsync(j->h_out, j->d_out, (uint64_t)j->n * 4, cudaMemcpyDeviceToHost, j->st));
     if (j->h_argmax) SERVE_TRY(cudaMemcpyAsync(j->h_argmax, j->d_am, 4, cudaMemcpyDeviceToHost, j->st));
-    SERVE_TRY(cudaEventRecord(j->done, j->st));
     return TN_OK;
+}
+
+void release_job(ServeJob *j)
+{
+    if (j->on) tn_online_destroy(j->on, j->st);
+    if (j->du) cudaFreeAsync(j->du, j->st);
+    if (j->dv) cudaFreeAsync(j->dv, j->st);
+    if (j->dt) cudaFreeAsync(j->dt, j->st);
+    if (j->d_out) cudaFreeAsync(j->d_out, j->st);
+    if (j->d_am) cudaFreeAsync(j->d_am, j->st);
+    if (j->st) cudaStreamSynchronize(j->st);
+    if (j->done) cudaEventDestroy(j->done);
+    if (j->st) cudaStreamDestroy(j->st);
 }
 
 void finish_job(tn_server *s, ServeJob *j)
 {
     j->t_done = now_ns();
-    // errors recorded by the kernels (batch order) live in the plans
-    for (tn_plan *p : j->plans) {
-        if (!p) continue;
-        const tn_status ps = tn_plan_status(p, j->st);
-        if (j->status == TN_OK && ps != TN_OK) j->status = ps;
-    }
+    // a device error of an applied batch is sticky in the online state
+    if (j->status == TN_OK && j->on) j->status = tn_online_status(j->on, j->st);
     tn_job_record r;
     memset(&r, 0, sizeof(r));
     r.job_id = j->id;
     r.status = j->status;
     r.n = j->n;
-    r.events = j->offs.back();
-    r.t_submit_ns = j->t_submit;
+    r.events = j->events;
+    r.t_submit_ns = j->t_open;
     r.t_admit_ns = j->t_admit;
     r.t_done_ns = j->t_done;
+    r.t_last_push_ns = j->t_last_push;
+    r.t_enqueued_ns = j->t_enqueued;
     release_job(j);
     {
         std::lock_guard<std::mutex> lock(s->mu);
@@ -224,63 +198,108 @@ void finish_job(tn_server *s, ServeJob *j)
     delete j;
 }
 
+// Admits the head of the queue if a slot and the memory are free.
+bool admit_one(tn_server *s)
+{
+    ServeJob *j = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        const uint64_t resident = s->active.size() + s->starting;
+        if (s->queue.empty() || resident >= s->opt.max_active) return false;
+        ServeJob *head = s->queue.front();
+        if (s->in_use + head->bytes > s->budget && resident > 0) return false;
+        s->queue.pop_front();
+        s->in_use += head->bytes;
+        s->admitted++;
+        s->starting++;
+        j = head;
+    }
+    j->t_admit = now_ns();
+    const tn_status rc = start_job(s, j);
+    std::lock_guard<std::mutex> lock(s->mu);
+    if (rc != TN_OK) j->status = rc;
+    s->starting--;
+    s->active.push_back(j);
+    if (s->active.size() > s->peak_active) s->peak_active = s->active.size();
+    if (s->in_use > s->peak_bytes) s->peak_bytes = s->in_use;
+    return true;
+}
+
+// Serves the next pending batch of some admitted job that no other worker is
+// serving.  A failed job drops its batches and finishes at its last one.
+bool serve_one(tn_server *s)
+{
+    ServeJob *j = nullptr;
+    ServeBatch b;
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        for (ServeJob *c : s->active) {
+            if (c->busy || c->finishing || c->batches.empty()) continue;
+            j = c;
+            b = c->batches.front();
+            c->batches.pop_front();
+            c->busy = true;
+            break;
+        }
+    }
+    if (!j) return false;
+    if (j->status == TN_OK) j->status = serve_batch(j, b);
+    if (b.last && j->done && j->st) cudaEventRecord(j->done, j->st);
+    std::lock_guard<std::mutex> lock(s->mu);
+    j->busy = false;
+    if (b.last) {
+        j->finishing = true;
+        j->t_enqueued = now_ns();
+    }
+    return true;
+}
+
+// Retires the admitted jobs whose results have reached the host.
+bool retire_done(tn_server *s)
+{
+    std::vector<ServeJob *> done;
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        for (size_t i = 0; i < s->active.size();) {
+            ServeJob *j = s->active[i];
+            const bool ready = j->finishing && !j->busy &&
+                               (!j->done || cudaEventQuery(j->done) != cudaErrorNotReady);
+            if (ready) {
+                done.push_back(j);
+                s->open.erase(j->id);
+                s->active[i] = s->active.back();
+                s->active.pop_back();
+            } else {
+                ++i;
+            }
+        }
+    }
+    for (ServeJob *j : done) finish_job(s, j);
+    return !done.empty();
+}
+
 void worker_loop(tn_server *s)
 {
     cudaSetDevice(s->device);
     for (;;) {
         bool progressed = false;
-        // admit in arrival order while a slot and the memory are free
-        for (;;) {
-            ServeJob *j = nullptr;
-            {
-                std::lock_guard<std::mutex> lock(s->mu);
-                const uint64_t resident = s->active.size() + s->starting;
-                if (s->queue.empty() || resident >= s->opt.max_active) break;
-                ServeJob *head = s->queue.front();
-                if (s->in_use + head->bytes > s->budget && resident > 0) break;
-                s->queue.pop_front();
-                s->in_use += head->bytes;
-                s->admitted++;
-                s->starting++;
-                j = head;
-            }
-            j->t_admit = now_ns();
-            j->status = start_job(s, j);
-            std::lock_guard<std::mutex> lock(s->mu);
-            s->starting--;
-            s->active.push_back(j);
-            if (s->active.size() > s->peak_active) s->peak_active = s->active.size();
-            if (s->in_use > s->peak_bytes) s->peak_bytes = s->in_use;
-            progressed = true;
+        while (admit_one(s)) progressed = true;
+        while (serve_one(s)) progressed = true;
+        progressed = retire_done(s) || progressed;
+        std::unique_lock<std::mutex> lock(s->mu);
+        if (s->stop && s->starting == 0) {
+            // after tn_server_destroy: run every job whose last batch was pushed
+            bool waiting = false;
+            for (ServeJob *q : s->queue) waiting = waiting || q->closed;
+            for (ServeJob *a : s->active) waiting = waiting || a->closed;
+            if (!waiting) return;
         }
-        // retire finished jobs
-        std::vector<ServeJob *> done;
-        {
-            std::lock_guard<std::mutex> lock(s->mu);
-            for (size_t i = 0; i < s->active.size();) {
-                ServeJob *j = s->active[i];
-                const bool ready = j->status != TN_OK || cudaEventQuery(j->done) != cudaErrorNotReady;
-                if (ready) {
-                    done.push_back(j);
-                    s->active[i] = s->active.back();
-                    s->active.pop_back();
-                } else {
-                    ++i;
-                }
-            }
-        }
-        for (ServeJob *j : done) finish_job(s, j);
-        progressed = progressed || !done.empty();
-        {
-            std::unique_lock<std::mutex> lock(s->mu);
-            if (s->stop && s->queue.empty() && s->active.empty() && s->starting == 0) return;
-            if (!progressed) {
-                if (s->active.empty()) {
-                    s->cv.wait_for(lock, std::chrono::milliseconds(5));
-                } else {
-                    lock.unlock();
-                    std::this_thread::sleep_for(std::chrono::microseconds(20));
-                }
+        if (!progressed) {
+            if (s->active.empty()) {
+                s->cv.wait_for(lock, std::chrono::milliseconds(2));
+            } else {
+                lock.unlock();
+                std::this_thread::sleep_for(std::chrono::microseconds(20));
             }
         }
     }
@@ -288,14 +307,22 @@ void worker_loop(tn_server *s)
 
 }  // namespace
 
+extern "C" uint64_t tn_server_job_bytes(uint32_t n, uint64_t max_batch_events)
+{
+    const uint64_t rows = ((uint64_t)n + 1023) / 1024 * 1024;
+    return rows * tn_row_words(n) * 8 + (uint64_t)n * 4 + 256 + max_batch_events * kBytesPerBatchEvent;
+}
+
 extern "C" tn_status tn_server_create(const tn_server_options *opt, tn_server **out)
 {
     if (!out) return TN_EINVAL;
     *out = nullptr;
+    if (opt && (opt->reserved[0] || opt->reserved[1])) return TN_EINVAL;
     tn_server *s = new (std::nothrow) tn_server();
     if (!s) return TN_ENOMEM;
     if (opt) s->opt = *opt;
     if (s->opt.max_active == 0) s->opt.max_active = 16;
+    if (s->opt.workers == 0) s->opt.workers = kDefaultWorkers;
     cudaError_t err = cudaGetDevice(&s->device);
     size_t free_b = 0, total_b = 0;
     if (err == cudaSuccess) err = cudaMemGetInfo(&free_b, &total_b);
@@ -306,11 +333,70 @@ extern "C" tn_status tn_server_create(const tn_server_options *opt, tn_server **
     }
     tn_internal_keep_pool();
     s->budget = s->opt.memory_budget ? s->opt.memory_budget : (uint64_t)(free_b * 0.6);
-    // several workers, so that copying in and scheduling one job (host
-    // synchronisations on its own stream) does not hold up the admission of
-    // the next ones
-    for (int w = 0; w < kServeWorkers; ++w) s->workers.emplace_back(worker_loop, s);
+    // several workers, so that copying in and scheduling one job's batch (host
+    // synchronisations on its own stream) does not hold up the others
+    for (uint32_t w = 0; w < s->opt.workers; ++w) s->workers.emplace_back(worker_loop, s);
     *out = s;
+    return TN_OK;
+}
+
+extern "C" tn_status tn_server_open(tn_server *s, uint64_t job_id, uint32_t n, uint64_t max_batch_events,
+                                    uint32_t *out_sizes, uint32_t *argmax)
+{
+    if (!s || n == 0 || n >= (1u << 30) || !out_sizes || max_batch_events >= (1ull << 30)) return TN_EINVAL;
+    ServeJob *j = new (std::nothrow) ServeJob();
+    if (!j) return TN_ENOMEM;
+    j->id = job_id;
+    j->n = n;
+    j->max_batch = max_batch_events;
+    j->h_out = out_sizes;
+    j->h_argmax = argmax;
+    j->bytes = tn_server_job_bytes(n, max_batch_events);
+    j->t_open = now_ns();
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        tn_status rc = TN_OK;
+        if (j->bytes > s->budget) rc = TN_ENOMEM;  // could never be admitted
+        else if (s->stop || s->open.count(job_id)) rc = TN_EINVAL;
+        if (rc != TN_OK) {
+            delete j;
+            return rc;
+        }
+        s->open[job_id] = j;
+        s->queue.push_back(j);
+    }
+    s->cv.notify_all();
+    return TN_OK;
+}
+
+extern "C" tn_status tn_server_push(tn_server *s, uint64_t job_id, const uint32_t *u, const uint32_t *v,
+                                    const int64_t *t, uint64_t m, uint32_t flags)
+{
+    if (!s || (flags & ~TN_LAST_BATCH) || (m > 0 && (!u || !v || !t))) return TN_EINVAL;
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        auto it = s->open.find(job_id);
+        if (it == s->open.end()) return TN_EINVAL;
+        ServeJob *j = it->second;
+        if (j->closed || m > j->max_batch) return TN_EINVAL;
+        ServeBatch b;
+        b.u = u;
+        b.v = v;
+        b.t = t;
+        b.m = m;
+        b.last = (flags & TN_LAST_BATCH) != 0;
+        try {
+            j->batches.push_back(b);
+        } catch (...) {
+            return TN_ENOMEM;
+        }
+        j->events += m;
+        if (b.last) {
+            j->closed = true;
+            j->t_last_push = now_ns();
+        }
+    }
+    s->cv.notify_all();
     return TN_OK;
 }
 
@@ -321,54 +407,20 @@ extern "C" tn_status tn_server_submit(tn_server *s, uint64_t job_id, uint32_t n,
     if (!s || n == 0 || n >= (1u << 30) || !batch_offsets || nbatches == 0 || !out_sizes) return TN_EINVAL;
     const uint64_t m = batch_offsets[nbatches];
     if (batch_offsets[0] != 0 || (m > 0 && (!u || !v || !t))) return TN_EINVAL;
-    for (uint32_t b = 0; b < nbatches; ++b)
-        if (batch_offsets[b + 1] < batch_offsets[b]) return TN_EINVAL;
-    std::vector<uint64_t> offs;
-    try {
-        offs.assign(batch_offsets, batch_offsets + nbatches + 1);
-    } catch (...) {
-        return TN_ENOMEM;
-    }
-    // A timestamp group is one snapshot (Section 2.1), so it must be applied
-    // whole: a batch boundary inside a group moves to the group's end, and the
-    // group is applied with the next batch (as the online state holds it back).
-    for (uint32_t b = 1; b < nbatches; ++b) {
-        uint64_t x = offs[b] > offs[b - 1] ? offs[b] : offs[b - 1];
-        while (x > 0 && x < m && t[x] == t[x - 1]) ++x;
-        offs[b] = x;
-    }
     uint64_t max_batch = 0;
     for (uint32_t b = 0; b < nbatches; ++b) {
-        const uint64_t mb = offs[b + 1] - offs[b];
+        if (batch_offsets[b + 1] < batch_offsets[b]) return TN_EINVAL;
+        const uint64_t mb = batch_offsets[b + 1] - batch_offsets[b];
         if (mb >= (1ull << 30)) return TN_EINVAL;
         if (mb > max_batch) max_batch = mb;
     }
-    ServeJob *j = new (std::nothrow) ServeJob();
-    if (!j) return TN_ENOMEM;
-    j->id = job_id;
-    j->n = n;
-    j->hu = u;
-    j->hv = v;
-    j->ht = t;
-    j->offs.swap(offs);
-    j->h_out = out_sizes;
-    j->h_argmax = argmax;
-    j->bytes = job_bytes(n, m, max_batch);
-    j->t_submit = now_ns();
-    {
-        std::lock_guard<std::mutex> lock(s->mu);
-        if (j->bytes > s->budget) {
-            delete j;
-            return TN_ENOMEM;  // could never be admitted
-        }
-        if (s->stop) {
-            delete j;
-            return TN_EINVAL;
-        }
-        s->queue.push_back(j);
+    tn_status rc = tn_server_open(s, job_id, n, max_batch, out_sizes, argmax);
+    for (uint32_t b = 0; b < nbatches && rc == TN_OK; ++b) {
+        const uint64_t e0 = batch_offsets[b];
+        rc = tn_server_push(s, job_id, u + e0, v + e0, t + e0, batch_offsets[b + 1] - e0,
+                            b + 1 == nbatches ? TN_LAST_BATCH : 0u);
     }
-    s->cv.notify_all();
-    return TN_OK;
+    return rc;
 }
 
 extern "C" tn_status tn_server_poll(tn_server *s, tn_job_record *records, uint32_t capacity, uint32_t *count,
@@ -413,6 +465,13 @@ extern "C" tn_status tn_server_destroy(tn_server *s)
     s->cv.notify_all();
     for (std::thread &w : s->workers)
         if (w.joinable()) w.join();
+    // jobs that never received their last batch (never admitted, or admitted
+    // and waiting): their matrices are released without results
+    for (auto &kv : s->open) {
+        ServeJob *j = kv.second;
+        release_job(j);
+        delete j;
+    }
     delete s;
     return TN_OK;
 }

@@ -21,6 +21,8 @@ __all__ = [
     "activity_driven",
     "powerlaw_bursty",
     "er_poisson",
+    "er_links",
+    "er_poisson_stream",
     "serving_jobs",
     "job_events",
     "split_batches",
@@ -144,13 +146,8 @@ def powerlaw_bursty(n: int, m: int, gamma: float = 2.5, k_min: int = 1,
             np.ascontiguousarray(t, dtype=np.int64))
 
 
-def er_poisson(n: int, m: int, p: float | None = None, seed: int = 0,
-               ticks_per_unit: float = 1e6):
-    """Erdos-Renyi G(n, p) (default p = 2/n) with an independent unit-rate Poisson
-    process on every link, as in the paper's synthetic experiments (Section 3.5).
-    The superposed process is simulated directly: each event picks a uniform
-    link and gaps are exponential with mean 1/|links|.  Times are integer ticks."""
-    rng = np.random.default_rng(seed)
+def _draw_er_links(rng, n, p):
+    """A binomial number of distinct pairs a < b, drawn uniformly (G(n, p))."""
     if p is None:
         p = 2.0 / n
     n_pairs = n * (n - 1) // 2
@@ -165,11 +162,59 @@ def er_poisson(n: int, m: int, p: float | None = None, seed: int = 0,
                 links.add((min(x, y), max(x, y)))
                 if len(links) == n_links:
                     break
-    links = np.array(sorted(links), dtype=np.int64).reshape(-1, 2)
+    return np.array(sorted(links), dtype=np.int64).reshape(-1, 2)
+
+
+def er_poisson(n: int, m: int, p: float | None = None, seed: int = 0,
+               ticks_per_unit: float = 1e6):
+    """Erdos-Renyi G(n, p) (default p = 2/n) with an independent unit-rate Poisson
+    process on every link, as in the paper's synthetic experiments (Section 3.5).
+    The superposed process is simulated directly: each event picks a uniform
+    link and gaps are exponential with mean 1/|links|.  Times are integer ticks."""
+    rng = np.random.default_rng(seed)
+    links = _draw_er_links(rng, n, p)
     pick = rng.integers(0, len(links), size=m)
     gaps = rng.exponential(1.0 / len(links), size=m)
     t = np.floor(np.cumsum(gaps) * ticks_per_unit).astype(np.int64)
     return _finish(links[pick, 0], links[pick, 1], t)
+
+
+def er_links(n: int, p: float | None = None, seed: int = 0) -> np.ndarray:
+    """The links (a < b) of an Erdos-Renyi G(n, p) draw, p = 2/n by default,
+    drawn exactly as ``er_poisson`` draws them for the same seed."""
+    return _draw_er_links(np.random.default_rng(seed), n, p)
+
+
+def er_poisson_stream(n: int, m: int, chunk: int = 100_000_000, p: float | None = None, seed: int = 0,
+                      ticks_per_unit: float = 1e6):
+    """The ER G(n, p) + per-link Poisson model of ``er_poisson`` (same links for
+    the same seed) as a stream of about ``chunk`` events at a time, for event
+    counts too large to hold at once.  The superposed process continues across
+    chunks (one running clock); every yielded chunk ends at a timestamp-group
+    boundary (the events of its last timestamp are held back and lead the next
+    chunk), so chunk k + 1 starts strictly after chunk k ends.  Yields
+    (u, v, t) arrays, m events in total."""
+    links = er_links(n, p, seed)
+    rng = np.random.default_rng([seed, 1])
+    clock, done = 0.0, 0
+    held = None
+    while done < m:
+        c = min(chunk, m - done)
+        pick = rng.integers(0, len(links), size=c)
+        gaps = rng.exponential(1.0 / len(links), size=c)
+        times = clock + np.cumsum(gaps)
+        clock = float(times[-1])
+        u, v = links[pick, 0].astype(np.uint32), links[pick, 1].astype(np.uint32)
+        t = np.floor(times * ticks_per_unit).astype(np.int64)
+        done += c
+        if held is not None:
+            u, v, t = np.concatenate([held[0], u]), np.concatenate([held[1], v]), np.concatenate([held[2], t])
+        if done < m:
+            cut = int(np.searchsorted(t, t[-1], side="left"))  # the last timestamp group stays behind
+            held = (u[cut:], v[cut:], t[cut:])
+            u, v, t = u[:cut], v[:cut], t[:cut]
+        if len(t):
+            yield u, v, t
 
 
 def serving_jobs(n_jobs: int, rate: float = 200.0, n_range=(10**3, 10**5),
@@ -189,9 +234,19 @@ def serving_jobs(n_jobs: int, rate: float = 200.0, n_range=(10**3, 10**5),
 
 
 def job_events(job: dict):
-    """Events of one serving job: uniform endpoints (u != v) and uniform integer
-    timestamps in [0, m), so equal-timestamp groups average one event."""
-    return uniform_events(job["n"], job["m"], t_range=max(1, job["m"]), seed=job["seed"])
+    """Events of one serving job: uniform endpoints (u != v) and integer
+    timestamps spread uniformly over [0, about m), so equal-timestamp groups
+    average one event.  The endpoints are independent of the times, so the
+    sorted times are drawn directly, with no sort of m values: the m events of
+    a unit-rate Poisson process (exponential gaps), floored to integer ticks,
+    so the number of events at each tick is Poisson with mean 1."""
+    rng = np.random.default_rng(job["seed"])
+    n, m = job["n"], job["m"]
+    u = rng.integers(0, n, size=m, dtype=np.int64)
+    v = (u + rng.integers(1, n, size=m, dtype=np.int64)) % n if n > 1 else u.copy()
+    t = np.floor(np.cumsum(rng.exponential(1.0, size=m))).astype(np.int64)
+    return (np.ascontiguousarray(u, dtype=np.uint32), np.ascontiguousarray(v, dtype=np.uint32),
+            np.ascontiguousarray(t, dtype=np.int64))
 
 
 def split_batches(t: np.ndarray, parts: int = 4):

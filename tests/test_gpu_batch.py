@@ -104,3 +104,27 @@ def test_autotune_keeps_results(n, m, replicas):
     if n * m <= 1e10:
         want = oracle.column_counts(oracle.component_matrix(u, v, t, n), n)
         assert np.array_equal(out_a.cpu().numpy().view(np.uint32), want)
+
+
+def test_batch_with_source_columns_and_wide_slabs():
+    """One launch over full matrices and column subsets (the hashed workload's
+    proxies together with its sampled exact columns), at different slab widths
+    and a wave spread: every matrix equals the oracle's."""
+    n, m = 3000, 40_000
+    u, v, t = synth.activity_driven(n, m, seed=17)
+    du, dv, dt = dev(u), dev(v), dev(t, np.int64)
+    rng = np.random.default_rng(17)
+    src_np = np.sort(rng.choice(n, 700, replace=False)).astype(np.uint32)
+    src2_np = rng.integers(0, n, 150).astype(np.uint32)  # repeated ids allowed
+    plans = [tn.Plan(du, dv, dt, n, slab_words=16), tn.Plan(du, dv, dt, n, slab_words=8, smem_rows=640),
+             tn.Plan(du, dv, dt, n, slab_words=2), tn.Plan(du, dv, dt, n, slab_words=32, wave_ctas=3)]
+    ncols = [n, 700, 150, n]
+    srcs = [None, dev(src_np), dev(src2_np), None]
+    mats = [torch.empty((n, tn.tn_row_words(c)), dtype=torch.int64, device="cuda") for c in ncols]
+    tn.tn_plan_apply_batch(plans, mats, ncols=ncols, init=True, srcs=srcs)
+    torch.cuda.synchronize()
+    full = oracle.component_matrix(u, v, t, n)
+    want = [full, oracle.component_matrix(u, v, t, n, src_np), oracle.component_matrix(u, v, t, n, src2_np), full]
+    for p, S, c, ref in zip(plans, mats, ncols, want):
+        assert p.status() == 0
+        assert np.array_equal(host(S, c), ref)

@@ -596,3 +596,60 @@ def test_directed_incremental_batches():
         tn.tn_component_matrix(du, dv, dt, n, S=S, t_last=t_last, init=(k == 0), directed=True)
     torch.cuda.synchronize()
     assert np.array_equal(host_matrix(S, n), oracle.component_matrix_directed(u, v, t, n))
+
+
+# --------------------------------------------------------------------------
+# the paper's synthetic experiments (Sections 3.5 and 4.4): ER G(n, 2/n)
+# with an independent Poisson process on every link
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("n,m", [(100, 20_000), (500, 50_000), (2000, 100_000)])
+def test_er_poisson_exact_and_hashed(n, m):
+    """The exact matrix and sizes, and the hashed estimate with n_s = 0.3 n
+    super-nodes and K = 5 replicas (the sweep's settings), bit-exact to the
+    oracle on the paper's generator; the error statistics as the sweep
+    reports them, against the oracle's."""
+    u, v, t = synth.er_poisson(n, m, seed=60 + n)
+    du, dv, dt = dev_events(u, v, t)
+    S = tn.tn_component_matrix(du, dv, dt, n)
+    exact, _, am = tn.tn_out_sizes(S, n, n, argmax=True)
+    ref = oracle.component_matrix(u, v, t, n)
+    assert np.array_equal(host_matrix(S, n), ref)
+    want_exact = oracle.column_counts(ref, n)
+    assert np.array_equal(u32(exact), want_exact) and int(am.item()) == oracle.argmax(want_exact)
+    k, K = max(1, int(0.3 * n)), 5
+    H, pu, pv = tn.tn_hash_proxy(du, dv, n, k, K, 6)
+    plans = [tn.Plan(pu[j].contiguous(), pv[j].contiguous(), dt, k) for j in range(K)]
+    P = torch.empty((K, k, tn.tn_row_words(k)), dtype=torch.int64, device="cuda")
+    tn.tn_plan_apply_batch(plans, [P[j] for j in range(K)])
+    est = tn.tn_hash_estimate(P, K, k, H, n)
+    err = tn.tn_error_stats(est, exact, n)
+    Href = oracle.hash_nodes(6, K, k, n)
+    Pref = oracle.proxy_matrices(u, v, t, Href, k)
+    want_est = oracle.hash_estimate(Pref, Href, n)
+    assert np.array_equal(u32(est), want_est)
+    want_err = oracle.error_stats(want_est, want_exact)
+    assert err["max_abs"] == want_err["max_abs"] and err["w1_num"] == want_err["w1_num"]
+    assert abs(err["w1"] - want_err["w1"]) <= 1e-12 * max(1.0, want_err["w1"])
+
+
+@pytest.mark.parametrize("n,m,t_range,window,smem_rows", [
+    (300, 20_000, 50, 640, 0),        # groups of ~400 events, every node ~2.7 times per group
+    (300, 20_000, 50, 4096, 1),       # the same through global windows
+    (5000, 60_000, 300, 640, 0),      # groups of ~200, few repeats
+    (40, 9_000, 3, 2048, 0),          # three giant groups on 40 nodes: long PULL lists, saved rows
+    (2000, 30_000, 200, 64, 0),       # windows smaller than a group
+])
+def test_large_groups_scheduled_by_the_whole_cta(n, m, t_range, window, smem_rows):
+    """Timestamp groups of 128 events or more are scheduled by every thread of
+    the planner's CTA (roles, runs, saved rows and source lists through
+    shared-memory atomics); the matrix must equal the oracle's."""
+    u, v, t = synth.uniform_events(n, m, t_range=t_range, seed=n + t_range)
+    du, dv, dt = dev_events(u, v, t)
+    for slab in (16, 64):
+        plan = tn.Plan(du, dv, dt, n, window_events=window, slab_words=slab, smem_rows=smem_rows)
+        st = plan.stats()
+        assert st["temps"] > 0 or t_range >= 300
+        S = torch.empty((n, tn.tn_row_words(n)), dtype=torch.int64, device="cuda")
+        plan.apply(S, init=True)
+        assert plan.status() == 0
+        assert np.array_equal(host_matrix(S, n), oracle.component_matrix(u, v, t, n)), slab

@@ -1,8 +1,9 @@
 """Serving engine (tn_server_*, needs a GPU: -m gpu).
 
 Each job's out-sizes must be bit-identical whether it runs alone or in a mix
-of concurrently admitted jobs, and identical to the one-shot host entry point
-and (for the small jobs) to the CPU oracle.
+of concurrently admitted jobs, whether its batches come all at once (submit)
+or one at a time while other jobs run (open + push), and identical to the
+one-shot host entry point and (for the small jobs) to the CPU oracle.
 """
 import time
 
@@ -70,12 +71,11 @@ def test_mix_equals_alone_and_one_shot():
 
 def test_admission_respects_memory_budget():
     jobs = make_jobs(8, seed=9, n_range=(3000, 3000), m_range=(20_000, 20_000))
-    # room for two of these jobs at a time: the engine charges each job its
-    # matrix, sizes, the schedules (16 B per event) and, per batch being
-    # scheduled, 80 B per event of the largest batch
-    def charge(n, offs):
-        return n * tn.tn_row_words(n) * 8 + n * 4 + 64 + int(np.diff(offs).max()) * 80 + int(offs[-1]) * 16
-    per_job = max(charge(n, offs) for _, n, _, _, _, offs in jobs)
+    # room for two of these jobs at a time (the charge of a job: its matrix,
+    # sizes and 160 B per event of its largest batch)
+    per_job = max(tn.tn_server_job_bytes(n, int(np.diff(offs).max())) for _, n, _, _, _, offs in jobs)
+    n0 = 3000
+    assert tn.tn_server_job_bytes(n0, 1000) == 3072 * tn.tn_row_words(n0) * 8 + n0 * 4 + 256 + 1000 * 160
     budget = int(2.5 * per_job)
     with tn.Server(memory_budget=budget, max_active=8) as srv:
         recs = run(srv, jobs)
@@ -122,9 +122,10 @@ def test_out_of_range_endpoint_is_reported():
 
 def test_batches_that_split_timestamp_groups():
     """Batch boundaries inside timestamp groups (Section 2.1: a group is one
-    snapshot) are moved to the groups' ends, so every group is applied whole:
-    the out-sizes equal the one-shot call and the oracle.  One job has a single
-    giant group spanning several batches (its later batches become empty)."""
+    snapshot): the job's online state holds a split group back until it is
+    complete, so every group is applied whole: the out-sizes equal the
+    one-shot call and the oracle.  One job has a single giant group spanning
+    every batch."""
     jobs = []
     for jid, (n, m, t_range) in enumerate([(400, 6000, 60), (900, 12_000, 300), (300, 3000, 1)], start=50):
         u, v, t = synth.uniform_events(n, m, t_range=t_range, seed=jid)
@@ -141,3 +142,67 @@ def test_batches_that_split_timestamp_groups():
         assert np.array_equal(results[jid][0], tn.tn_out_component_sizes_host(u, v, t, n)[0]), jid
         want = oracle.column_counts(oracle.component_matrix(u, v, t, n), n)
         assert np.array_equal(results[jid][0], want), jid
+
+
+def test_incremental_batches_while_other_jobs_run():
+    """Jobs opened at staggered times receive their 4 batches one at a time,
+    with pauses between them, while other jobs are resident: every job's
+    out-sizes equal the one-shot call (and the oracle for small jobs), and
+    the records show at least two jobs resident at the same time."""
+    jobs = make_jobs(10, seed=21, n_range=(500, 8000), m_range=(20_000, 300_000))
+    with tn.Server(max_active=6, workers=4) as srv:
+        pending = []
+        for jid, n, u, v, t, offs in jobs:
+            srv.open(jid, n, int(np.diff(offs).max()))
+            pending.append((jid, u, v, t, offs, 0))
+        while pending:
+            nxt = []
+            for jid, u, v, t, offs, b in pending:
+                a, e = int(offs[b]), int(offs[b + 1])
+                srv.push(jid, u[a:e], v[a:e], t[a:e], last=b + 2 == len(offs))
+                if b + 2 < len(offs):
+                    nxt.append((jid, u, v, t, offs, b + 1))
+            pending = nxt
+            time.sleep(0.02)
+        recs, deadline = [], time.time() + 120
+        while len(recs) < len(jobs) and time.time() < deadline:
+            recs += srv.poll(wait_ms=50)
+        results = dict(srv.results)
+        st = srv.stats()
+    assert len(recs) == len(jobs)
+    by_id = {r["job_id"]: r for r in recs}
+    for jid, n, u, v, t, offs in jobs:
+        r = by_id[jid]
+        assert r["status"] == 0 and r["events"] == len(u)
+        assert r["t_submit_ns"] <= r["t_admit_ns"] <= r["t_enqueued_ns"] <= r["t_done_ns"]
+        assert r["t_last_push_ns"] <= r["t_enqueued_ns"]
+        assert np.array_equal(results[jid][0], tn.tn_out_component_sizes_host(u, v, t, n)[0]), jid
+        if n * len(u) <= 5e8:
+            want = oracle.column_counts(oracle.component_matrix(u, v, t, n), n)
+            assert np.array_equal(results[jid][0], want), jid
+    # resident at once: admission-to-results intervals that overlap
+    spans = sorted((r["t_admit_ns"], r["t_done_ns"]) for r in recs)
+    most = max(sum(1 for a, b in spans if a <= s0 < b) for s0, _ in spans)
+    assert most >= 2 and st["peak_active"] >= 2
+
+
+def test_push_errors():
+    with tn.Server(max_active=2) as srv:
+        srv.open(1, 100, 10)
+        u = np.zeros(11, np.uint32); v = np.ones(11, np.uint32); t = np.arange(11, dtype=np.int64)
+        with pytest.raises(tn.TnError):
+            srv.push(1, u, v, t)  # more events than the job's bound
+        with pytest.raises(tn.TnError):
+            srv.push(2, u[:3], v[:3], t[:3])  # never opened
+        with pytest.raises(tn.TnError):
+            srv.open(1, 100, 10)  # already open
+        srv.push(1, u[:5], v[:5], t[:5])
+        srv.push(1, u[5:10], v[5:10], t[5:10], last=True)
+        with pytest.raises(tn.TnError):
+            srv.push(1, u[:1], v[:1], t[:1] + 100)  # after the last batch
+        recs, deadline = [], time.time() + 30
+        while not recs and time.time() < deadline:
+            recs += srv.poll(wait_ms=50)
+        assert recs[0]["job_id"] == 1 and recs[0]["status"] == 0
+        sizes = srv.results[1][0]
+    assert np.array_equal(sizes, tn.tn_out_component_sizes_host(u[:10], v[:10], t[:10], 100)[0])

@@ -48,6 +48,9 @@ def test_host_helpers_without_gpu(lib_path):
     assert tn.tn_row_words(100_000) == 1568
     assert tn.tn_status_string(tn.TN_ERANGE).startswith("TN_ERANGE")
     assert tn.tn_status_string(12345) == "unknown tn_status"
+    # serving charge: matrix rows rounded up to 1,024, sizes, 256 B, 160 B per event of the largest batch
+    assert tn.tn_server_job_bytes(3000, 1000) == 3072 * 48 * 8 + 3000 * 4 + 256 + 1000 * 160
+    assert tn.tn_server_job_bytes(1024, 0) == 1024 * 16 * 8 + 1024 * 4 + 256
 
 
 def test_binding_fails_loudly_without_library(tmp_path):
