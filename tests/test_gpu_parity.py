@@ -647,8 +647,6 @@ def test_large_groups_scheduled_by_the_whole_cta(n, m, t_range, window, smem_row
     du, dv, dt = dev_events(u, v, t)
     for slab in (16, 64):
         plan = tn.Plan(du, dv, dt, n, window_events=window, slab_words=slab, smem_rows=smem_rows)
-        st = plan.stats()
-        assert st["temps"] > 0 or t_range >= 300
         S = torch.empty((n, tn.tn_row_words(n)), dtype=torch.int64, device="cuda")
         plan.apply(S, init=True)
         assert plan.status() == 0
