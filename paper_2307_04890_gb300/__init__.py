@@ -487,10 +487,10 @@ class Server:
             raise ValueError("batch offsets must end at the number of events")
         out = np.zeros(n, dtype=np.uint32)
         am = np.zeros(1, dtype=np.uint32)
-        self._keep[job_id] = [out, am, (u, v, t, offs)]
         _check(lib.tn_server_submit(self._h, job_id, n, u.ctypes.data, v.ctypes.data, t.ctypes.data,
                                     offs.ctypes.data, len(offs) - 1, out.ctypes.data, am.ctypes.data),
                "tn_server_submit")
+        self._keep[job_id] = [out, am, (u, v, t, offs)]
 
     def open(self, job_id: int, n: int, max_batch_events: int):
         """Opens a job whose batches (at most ``max_batch_events`` events each)
@@ -498,9 +498,9 @@ class Server:
         import numpy as np
         out = np.zeros(n, dtype=np.uint32)
         am = np.zeros(1, dtype=np.uint32)
-        self._keep[job_id] = [out, am]
         _check(load_library().tn_server_open(self._h, job_id, n, max_batch_events, out.ctypes.data, am.ctypes.data),
                "tn_server_open")
+        self._keep[job_id] = [out, am]  # only once the job is open: a refused open keeps the old job's buffers
 
     def push(self, job_id: int, u, v, t, last: bool = False):
         """Appends a batch of host events to an open job (``last``: the job's
@@ -511,9 +511,9 @@ class Server:
         t = np.ascontiguousarray(t, dtype=np.int64)
         if len(v) != len(u) or len(t) != len(u):
             raise ValueError("u, v and t must have the same length")
-        self._keep.setdefault(job_id, [None, None]).append((u, v, t))
         _check(load_library().tn_server_push(self._h, job_id, u.ctypes.data, v.ctypes.data, t.ctypes.data, len(u),
                                              TN_LAST_BATCH if last else 0), "tn_server_push")
+        self._keep[job_id].append((u, v, t))  # alive until the job's record is polled
 
     def poll(self, wait_ms: int = 0, capacity: int = 256):
         """Records of finished jobs: dicts with job_id, status, n, events and

@@ -415,10 +415,26 @@ extern "C" tn_status tn_server_submit(tn_server *s, uint64_t job_id, uint32_t n,
         if (mb > max_batch) max_batch = mb;
     }
     tn_status rc = tn_server_open(s, job_id, n, max_batch, out_sizes, argmax);
+    if (rc != TN_OK) return rc;
     for (uint32_t b = 0; b < nbatches && rc == TN_OK; ++b) {
         const uint64_t e0 = batch_offsets[b];
         rc = tn_server_push(s, job_id, u + e0, v + e0, t + e0, batch_offsets[b + 1] - e0,
                             b + 1 == nbatches ? TN_LAST_BATCH : 0u);
+    }
+    if (rc != TN_OK) {
+        // the job ends with this error: its pushed batches are dropped unread
+        // (the caller is told to release its buffers) and its record reports rc
+        std::lock_guard<std::mutex> lock(s->mu);
+        auto it = s->open.find(job_id);
+        if (it != s->open.end()) {
+            ServeJob *j = it->second;
+            j->status = rc;
+            j->batches.clear();
+            j->closed = true;
+            ServeBatch end;
+            end.last = true;
+            j->batches.push_back(end);
+        }
     }
     return rc;
 }
