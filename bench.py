@@ -48,6 +48,10 @@ PROFILE_SUMMARIES = {"activity": ("stream_kernel_activity_n1e5_m1e7.txt", STREAM
 WORKLOADS = {
     "activity": dict(desc="activity-driven n=100000 m=10000000 (power-law activity 2.1, a_min 1e-3, us ticks)",
                      kind="activity", n=100_000, m=10_000_000, seed=2),
+    "bursty-scaled": dict(desc="profiling case of the bursty launch: the first 2000000 events of the bursty "
+                               "n=500000 stream with node ids folded mod 40000, 503808 source columns (each node "
+                               "12.6 times), 64-word slabs: 123 CTAs as in the full launch, a 2.5 GB matrix",
+                          kind="scaled", n=40_000, m=2_000_000, seed=3, ncols=123 * 64 * 64, slab=64),
     "uniform-small": dict(desc="uniform pairs n=1000 m=20000, t uniform in [0,1e4)", kind="uniform",
                           n=1000, m=20_000, seed=1, t_range=10_000),
     "bursty": dict(desc="power-law bursty n=500000 m=100000000 (degree exponent 2.5, Pareto(1.5, 60 s) gaps, "
@@ -84,7 +88,7 @@ def parse_args():
     ap.add_argument("--distinct-jobs", type=int, default=200, help="serving: distinct event sets the jobs cycle")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
     ap.add_argument("--batch-gap-ms", type=float, default=20.0, help="serving: time between a job's batches")
-    ap.add_argument("--max-active", type=int, default=16, help="serving: jobs resident at once")
+    ap.add_argument("--max-active", type=int, default=64, help="serving: jobs resident at once")
     ap.add_argument("--workers", type=int, default=8, help="serving: host worker threads of the server")
     return ap.parse_args()
 
@@ -437,6 +441,54 @@ def run_reference(args, w, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_scaled(args, w, rank, world, local_rank):
+    """The bursty launch at a size an ncu --set full capture can replay: the
+    same 123 CTAs of 64-word slabs and global-memory windows, on a 2.5 GB
+    matrix (node ids folded, source ids repeated).  One step = init + stream."""
+    import torch
+    import paper_2307_04890_gb300 as tn
+    from paper_2307_04890_gb300 import synth
+    from paper_2307_04890_gb300.build import build_library
+
+    build_library()
+    tn.load_library()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    n, m, ncols = w["n"], w["m"], w["ncols"]
+    u, v, t = synth.powerlaw_bursty(500_000, 100_000_000, seed=w["seed"])
+    u, v, t = (u[:m] % n).astype(np.uint32), (v[:m] % n).astype(np.uint32), t[:m]
+    du = torch.from_numpy(u.view(np.int32)).to(dev)
+    dv = torch.from_numpy(v.view(np.int32)).to(dev)
+    dt = torch.from_numpy(t).to(dev)
+    src = torch.from_numpy((np.arange(ncols) % n).astype(np.int32)).to(dev)
+    plan = tn.Plan(du, dv, dt, n, slab_words=w["slab"])
+    S = torch.empty((n, tn.tn_row_words(ncols)), dtype=torch.int64, device=dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    for _ in range(args.warmup):
+        plan.apply(S, ncols=ncols, src=src, init=True)
+    times = []
+    for _ in range(args.steps):
+        e0, e1 = ev(), ev()
+        e0.record()
+        plan.apply(S, ncols=ncols, src=src, init=True)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    assert plan.status() == 0
+    ms = statistics.mean(times)
+    alg = m * 4 * (ncols // 64) * 8
+    peak, _ = measured_peaks()
+    if rank == 0:
+        print(json.dumps({"metric": "bit-updates/s of the scaled bursty launch (profiling case)",
+                          "value": ncols * m / (ms * 1e-3), "unit": "bit-updates/s", "n_gpus": 1,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                          "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+                          "config": {"workload": w["desc"], "plan": plan.stats()},
+                          "roofline": {"bound": "hbm", "achieved": alg / (ms * 1e-3) / 1e9, "peak": peak,
+                                       "unit": "GB/s", "frac": alg / (ms * 1e-3) / 1e9 / peak, "traffic": None,
+                                       "algorithmic_bytes_per_launch": alg}}), flush=True)
+
+
 def run_serving(args, w, rank, world, local_rank):
     """Continuous admission of a Poisson stream of jobs through tn_server_*.
     Job j opens at its arrival time and its 4 batches (split at timestamp
@@ -625,9 +677,12 @@ def run_hashed(args, w, rank, world, local_rank):
     ms_total = job_max_ms(start.elapsed_time(end), dist, dev)
     ms_step = ms_total / args.steps
 
-    # the same work in separate launches, and the proxies as a graph vs one launch each
+    # the same work in separate launches, each at its own best shape (the proxies alone:
+    # 8-word slabs in 80 KB row buffers, two 4-warp CTAs per SM; the exact columns:
+    # the defaults), and the proxies as a graph vs one launch each
     P_ref, Sx_ref = P.clone(), Sx.clone()
-    plans = [tn.Plan(pu[j].contiguous(), pv[j].contiguous(), dt, k, **popts) for j in range(R)]
+    sopts = dict(slab_words=8, window_events=640, smem_rows=80 * 1024 // (8 * 8))
+    plans = [tn.Plan(pu[j].contiguous(), pv[j].contiguous(), dt, k, **sopts) for j in range(R)]
     plan_x = tn.Plan(du, dv, dt, n, **xopts)
     e0, e1, e2 = ev(), ev(), ev()
     e0.record(stream)
@@ -660,18 +715,24 @@ def run_hashed(args, w, rank, world, local_rank):
     plan_x.destroy()
     del P2, P_ref, Sx_ref
 
-    # error on an unsaturated prefix: the first 10^6 events (to a group boundary)
-    mp = group_prefix(t, 1_000_000)
-    Hp, pup, pvp = tn.tn_hash_proxy(du[:mp], dv[:mp], n, k, R, seed)
-    plans_p = [tn.Plan(pup[j].contiguous(), pvp[j].contiguous(), dt[:mp], k, **popts) for j in range(R)]
-    plan_xp = tn.Plan(du[:mp], dv[:mp], dt[:mp], n, **xopts)
-    tn.tn_plan_apply_batch(plans_p + [plan_xp], [P[j] for j in range(R)] + [Sx], ncols=[k] * R + [nsrc],
-                           init=True, srcs=[None] * R + [src])
-    est_p = tn.tn_hash_estimate(P, R, k, Hp, n, src=src)
-    exact_p, _, _ = tn.tn_out_sizes(Sx, n, nsrc)
-    err_p = tn.tn_error_stats(est_p, exact_p, n)
-    for p in plans_p + [plan_xp]:
-        p.destroy()
+    # error on unsaturated prefixes of the stream (to a group boundary)
+    keys = ("mean_abs", "max_abs", "mean_rel", "max_rel", "w1")
+    prefixes = []
+    for want in (10_000, 100_000, 1_000_000):
+        mp = group_prefix(t, want)
+        Hp, pup, pvp = tn.tn_hash_proxy(du[:mp], dv[:mp], n, k, R, seed)
+        plans_p = [tn.Plan(pup[j].contiguous(), pvp[j].contiguous(), dt[:mp], k, **popts) for j in range(R)]
+        plan_xp = tn.Plan(du[:mp], dv[:mp], dt[:mp], n, **xopts)
+        tn.tn_plan_apply_batch(plans_p + [plan_xp], [P[j] for j in range(R)] + [Sx], ncols=[k] * R + [nsrc],
+                               init=True, srcs=[None] * R + [src])
+        est_p = tn.tn_hash_estimate(P, R, k, Hp, n, src=src)
+        exact_p, _, _ = tn.tn_out_sizes(Sx, n, nsrc)
+        err_p = tn.tn_error_stats(est_p, exact_p, n)
+        prefixes.append(dict({key: err_p[key] for key in keys}, events=mp,
+                             mean_exact=float(exact_p.float().mean().item()),
+                             mean_estimate=float(est_p.float().mean().item())))
+        for p in plans_p + [plan_xp]:
+            p.destroy()
 
     combined_ms = statistics.mean(timing["combined_ms"])
     wx = tn.tn_row_words(nsrc)
@@ -679,7 +740,6 @@ def run_hashed(args, w, rank, world, local_rank):
     alg_proxy = R * m * 4 * ((k + 63) // 64) * 8
     peak, peak_kind = measured_peaks()
     bit_updates = (R * k + nsrc) * m
-    keys = ("mean_abs", "max_abs", "mean_rel", "max_rel", "w1")
     result = {"metric": METRIC + " (hashed estimate)", "value": world * m / (ms_step * 1e-3), "unit": "events/s",
               "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
@@ -699,11 +759,10 @@ def run_hashed(args, w, rank, world, local_rank):
                            "algorithmic_bytes_per_launch": alg_exact + alg_proxy,
                            "note": "the proxies' 32 MB matrices are served largely from L2"},
               "error": {key: err[key] for key in keys},
-              "error_prefix": dict({key: err_p[key] for key in keys}, events=mp,
-                                   mean_exact=float(exact_p.float().mean().item()),
-                                   mean_estimate=float(est_p.float().mean().item())),
+              "error_prefixes": prefixes,
               "combined_vs_separate": {"combined_ms": combined_ms,
                                        "separate_ms": proxies_alone_ms + exact_alone_ms,
+                                       "separate_shapes": {"proxies": sopts, "exact_sampled": xopts},
                                        "identical": separate_identical},
               "batched_vs_single": {"graph_replay_ms": graph_ms, "single_launches_ms": single_ms,
                                     "identical": identical},
@@ -965,6 +1024,13 @@ def main():
         return
     if w["kind"] == "online" and args.impl == "ours":
         run_online(args, w, rank, world, local_rank)
+        return
+    if w["kind"] == "scaled":
+        if args.impl == "ours":
+            run_scaled(args, w, rank, world, local_rank)
+        elif rank == 0:
+            print(json.dumps({"impl": "reference", "unavailable": "a profiling case of the GPU launch, not a "
+                              "workload; its reference is the bursty workload's"}), flush=True)
         return
     if w["kind"] == "sweep":
         if args.impl == "ours":

@@ -262,6 +262,16 @@ constexpr uint32_t kApplyMax = 1u << 16;
 tn_status apply_jobs(const tn_plan *const *plans, uint64_t *const *S, const uint32_t *ncols,
                      const uint32_t *const *src, int64_t *const *t_last, uint32_t count, uint32_t flags,
                      cudaStream_t stream);
+// Online state in two-stream mode (used by the serving engine): its matrix
+// updates (and node growth) run on `apply_stream`, while the stream given to
+// each tn_online_push carries the copies and the scheduling, so scheduling a
+// batch never waits for the update of the one before.  Must be called right
+// after tn_online_create, with the matrix's initialisation complete on both
+// streams.  Up to kOnlineFlight applied batches stay in flight; a device error
+// of one is returned once that batch has finished, and always by
+// tn_online_status.
+constexpr uint32_t kOnlineFlight = 8;
+tn_status online_use_apply_stream(tn_online *online, cudaStream_t apply_stream);
 // Reversed copy of an event sequence (Section 3.4): event m-1-e becomes event e,
 // t -> ~t; with `turn` the endpoints are swapped (directed events).  The three
 // arrays come from the stream-ordered allocator; the caller frees them.

@@ -170,6 +170,14 @@ struct tn_online {
     ScanOut *scan;
     tn_plan *inflight;  // plan of the last applied batch, released at the next call
     uint64_t applied_events, batches;
+    // two-stream mode (tn::online_use_apply_stream): the matrix updates run on
+    // `ast` while copies and scheduling run on the caller's stream; the plans
+    // of applied batches are released once an event behind their update has
+    // completed, without waiting for it
+    cudaStream_t ast;
+    tn_plan *flight[tn::kOnlineFlight];
+    cudaEvent_t flight_done[tn::kOnlineFlight];
+    uint32_t flight_head, flight_count;
 };
 
 namespace {
@@ -186,9 +194,34 @@ bool on_device(const tn_online *o)
     return cudaGetDevice(&dev) == cudaSuccess && dev == o->device;
 }
 
+// Two-stream mode: releases the plans of applied batches whose update has
+// finished (all of them, waiting, with `wait`), folding their status into the
+// sticky error.
+tn_status reap(tn_online *o, bool wait)
+{
+    while (o->flight_count > 0) {
+        const uint32_t i = o->flight_head;
+        if (wait) {
+            cudaEventSynchronize(o->flight_done[i]);
+        } else {
+            const cudaError_t q = cudaEventQuery(o->flight_done[i]);
+            if (q == cudaErrorNotReady) break;
+        }
+        int32_t h = 0;
+        if (cudaMemcpy(&h, o->flight[i]->d_status, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) h = TN_ECUDA;
+        if (h != TN_OK && o->error == TN_OK) o->error = h;
+        tn_plan_destroy(o->flight[i], o->ast);
+        cudaEventDestroy(o->flight_done[i]);
+        o->flight_head = (i + 1) % tn::kOnlineFlight;
+        o->flight_count--;
+    }
+    return (tn_status)o->error;
+}
+
 // Waits for the last applied batch and folds its status into the sticky error.
 tn_status settle(tn_online *o, cudaStream_t st)
 {
+    if (o->ast) return reap(o, true);
     if (o->inflight) {
         const tn_status rc = tn_plan_status(o->inflight, st);
         tn_plan_destroy(o->inflight, st);
@@ -249,6 +282,35 @@ tn_status apply_ready(tn_online *o, const uint32_t *u, const uint32_t *v, const 
     tn_plan *plan = nullptr;
     tn_status rc = tn_plan_create(u, v, t, count, o->n, nullptr, &o->opt, st, &plan);
     if (rc != TN_OK) return rc;
+    if (o->ast) {
+        // the plan is complete (tn_plan_create returned), so the update may run
+        // on the apply stream behind the earlier ones
+        if (o->flight_count == tn::kOnlineFlight) {  // room in the ring: wait for the oldest update
+            cudaEventSynchronize(o->flight_done[o->flight_head]);
+            reap(o, false);
+        }
+        cudaEvent_t done = nullptr;
+        cudaError_t err = cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
+        if (err == cudaSuccess) {
+            rc = tn_plan_apply(plan, o->S, o->n, nullptr, nullptr, 0u, o->ast);
+            if (rc == TN_OK) err = cudaEventRecord(done, o->ast);
+        }
+        if (err != cudaSuccess || rc != TN_OK) {
+            if (done) cudaEventDestroy(done);
+            tn_plan_destroy(plan, o->ast);
+            if (err != cudaSuccess) {
+                tn_internal_set_cuda_error(err);
+                return TN_ECUDA;
+            }
+            return rc;
+        }
+        const uint32_t slot = (o->flight_head + o->flight_count) % tn::kOnlineFlight;
+        o->flight[slot] = plan;
+        o->flight_done[slot] = done;
+        o->flight_count++;
+        o->applied_events += count;
+        return TN_OK;
+    }
     rc = tn_plan_apply(plan, o->S, o->n, nullptr, nullptr, 0u, st);
     if (rc != TN_OK) {
         tn_plan_destroy(plan, st);
@@ -316,7 +378,7 @@ extern "C" tn_status tn_online_push(tn_online *o, const uint32_t *u, const uint3
     if (m > 0 && (!u || !v || !t)) return TN_EINVAL;
     if (m >= (1ull << 30) || o->pending + m >= (1ull << 30)) return TN_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
-    tn_status rc = settle(o, st);
+    tn_status rc = o->ast ? reap(o, false) : settle(o, st);
     if (rc != TN_OK) return rc;
 
     const uint64_t P = o->pending;  // events held back from the previous batch
@@ -404,8 +466,8 @@ extern "C" tn_status tn_online_flush(tn_online *o, void *stream)
 extern "C" tn_status tn_online_grow(tn_online *o, uint32_t n_new, void *stream)
 {
     if (!o || n_new < o->n || n_new >= (1u << 30) || !on_device(o)) return TN_EINVAL;
-    cudaStream_t st = (cudaStream_t)stream;
-    tn_status rc = settle(o, st);
+    cudaStream_t st = o->ast ? o->ast : (cudaStream_t)stream;  // the matrix lives on the apply stream
+    tn_status rc = o->ast ? reap(o, false) : settle(o, st);
     if (rc != TN_OK) return rc;
     if (n_new == o->n) return TN_OK;
     if (tn_row_words(n_new) == tn_row_words(o->n) && n_new <= o->row_cap) {
@@ -425,6 +487,13 @@ extern "C" tn_status tn_online_grow(tn_online *o, uint32_t n_new, void *stream)
         o->row_cap = cap;
     }
     o->n = n_new;
+    return TN_OK;
+}
+
+tn_status tn::online_use_apply_stream(tn_online *o, cudaStream_t apply_stream)
+{
+    if (!o || !apply_stream || o->ast || o->batches || o->inflight) return TN_EINVAL;
+    o->ast = apply_stream;
     return TN_OK;
 }
 
@@ -454,8 +523,9 @@ extern "C" tn_status tn_online_destroy(tn_online *o, void *stream)
 {
     if (!o) return TN_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
+    if (o->ast) reap(o, true);
     if (o->inflight) tn_plan_destroy(o->inflight, st);
-    cudaFreeAsync(o->S, st);
+    cudaFreeAsync(o->S, o->ast ? o->ast : st);
     cudaFreeAsync(o->scan, st);
     if (o->pu) cudaFreeAsync(o->pu, st);
     if (o->pv) cudaFreeAsync(o->pv, st);

@@ -66,8 +66,9 @@ struct ServeJob {
     bool busy = false;               // a worker is serving one of its batches
     bool finishing = false;          // results enqueued (or the job failed): retire when done
     uint64_t events = 0;
-    // device state, used by one worker at a time
-    cudaStream_t st = nullptr;
+    // device state, used by one worker at a time: copies in and scheduling on
+    // st, matrix updates, sizes and the copy back on ast
+    cudaStream_t st = nullptr, ast = nullptr;
     cudaEvent_t done = nullptr;
     tn_online *on = nullptr;
     uint32_t *du = nullptr, *dv = nullptr, *d_out = nullptr, *d_am = nullptr;
@@ -119,22 +120,35 @@ uint32_t serve_slab_words(uint32_t n)
     return sw < 2 ? 2u : (uint32_t)sw;
 }
 
-// Stream, online state, copy-in buffers and result buffers of an admitted job.
+// Streams, online state (two-stream mode), copy-in buffers and result buffers
+// of an admitted job.
 tn_status start_job(tn_server *s, ServeJob *j)
 {
     SERVE_TRY(cudaStreamCreateWithFlags(&j->st, cudaStreamNonBlocking));
+    SERVE_TRY(cudaStreamCreateWithFlags(&j->ast, cudaStreamNonBlocking));
     SERVE_TRY(cudaEventCreateWithFlags(&j->done, cudaEventDisableTiming));
     const uint64_t mb = j->max_batch ? j->max_batch : 1;
     SERVE_TRY(cudaMallocAsync((void **)&j->du, mb * 4, j->st));
     SERVE_TRY(cudaMallocAsync((void **)&j->dv, mb * 4, j->st));
     SERVE_TRY(cudaMallocAsync((void **)&j->dt, mb * 8, j->st));
-    SERVE_TRY(cudaMallocAsync((void **)&j->d_out, (uint64_t)j->n * 4, j->st));
-    SERVE_TRY(cudaMallocAsync((void **)&j->d_am, 4, j->st));
+    SERVE_TRY(cudaMallocAsync((void **)&j->d_out, (uint64_t)j->n * 4, j->ast));
+    SERVE_TRY(cudaMallocAsync((void **)&j->d_am, 4, j->ast));
     tn_plan_options opt;
     memset(&opt, 0, sizeof(opt));
     opt.window_events = s->opt.window_events;
     opt.slab_words = s->opt.slab_words ? s->opt.slab_words : serve_slab_words(j->n);
-    return tn_online_create(j->n, &opt, j->st, &j->on);
+    // a row buffer of 1,280 slots holds a default 640-event window (two rows per
+    // event): small jobs' narrow slabs then need 20-80 KB, so several of their
+    // CTAs share an SM
+    if (!s->opt.window_events && !s->opt.slab_words) opt.smem_rows = 1280;
+    tn_status rc = tn_online_create(j->n, &opt, j->ast, &j->on);
+    if (rc != TN_OK) return rc;
+    rc = tn::online_use_apply_stream(j->on, j->ast);
+    if (rc != TN_OK) return rc;
+    // the state's buffers and the copy-in buffers are ready for both streams
+    SERVE_TRY(cudaStreamSynchronize(j->ast));
+    SERVE_TRY(cudaStreamSynchronize(j->st));
+    return TN_OK;
 }
 
 // One batch of an admitted job: copy in, push to the online state, and after
@@ -151,23 +165,25 @@ tn_status serve_batch(ServeJob *j, const ServeBatch &b)
     tn_online_state state;
     rc = tn_online_get_state(j->on, &state);
     if (rc != TN_OK) return rc;
-    rc = tn_out_sizes(state.S, j->n, j->n, j->d_out, nullptr, j->d_am, j->st);
+    rc = tn_out_sizes(state.S, j->n, j->n, j->d_out, nullptr, j->d_am, j->ast);
     if (rc != TN_OK) return rc;
-    SERVE_TRY(cudaMemcpyAsync(j->h_out, j->d_out, (uint64_t)j->n * 4, cudaMemcpyDeviceToHost, j->st));
-    if (j->h_argmax) SERVE_TRY(cudaMemcpyAsync(j->h_argmax, j->d_am, 4, cudaMemcpyDeviceToHost, j->st));
+    SERVE_TRY(cudaMemcpyAsync(j->h_out, j->d_out, (uint64_t)j->n * 4, cudaMemcpyDeviceToHost, j->ast));
+    if (j->h_argmax) SERVE_TRY(cudaMemcpyAsync(j->h_argmax, j->d_am, 4, cudaMemcpyDeviceToHost, j->ast));
     return TN_OK;
 }
 
 void release_job(ServeJob *j)
 {
-    if (j->on) tn_online_destroy(j->on, j->st);
+    if (j->on) tn_online_destroy(j->on, j->st);  // waits for the updates in flight on ast
     if (j->du) cudaFreeAsync(j->du, j->st);
     if (j->dv) cudaFreeAsync(j->dv, j->st);
     if (j->dt) cudaFreeAsync(j->dt, j->st);
-    if (j->d_out) cudaFreeAsync(j->d_out, j->st);
-    if (j->d_am) cudaFreeAsync(j->d_am, j->st);
+    if (j->d_out) cudaFreeAsync(j->d_out, j->ast);
+    if (j->d_am) cudaFreeAsync(j->d_am, j->ast);
+    if (j->ast) cudaStreamSynchronize(j->ast);
     if (j->st) cudaStreamSynchronize(j->st);
     if (j->done) cudaEventDestroy(j->done);
+    if (j->ast) cudaStreamDestroy(j->ast);
     if (j->st) cudaStreamDestroy(j->st);
 }
 
@@ -175,7 +191,7 @@ void finish_job(tn_server *s, ServeJob *j)
 {
     j->t_done = now_ns();
     // a device error of an applied batch is sticky in the online state
-    if (j->status == TN_OK && j->on) j->status = tn_online_status(j->on, j->st);
+    if (j->status == TN_OK && j->on) j->status = tn_online_status(j->on, j->ast);
     tn_job_record r;
     memset(&r, 0, sizeof(r));
     r.job_id = j->id;
@@ -244,7 +260,7 @@ bool serve_one(tn_server *s)
     }
     if (!j) return false;
     if (j->status == TN_OK) j->status = serve_batch(j, b);
-    if (b.last && j->done && j->st) cudaEventRecord(j->done, j->st);
+    if (b.last && j->done && j->ast) cudaEventRecord(j->done, j->ast);
     std::lock_guard<std::mutex> lock(s->mu);
     j->busy = false;
     if (b.last) {
