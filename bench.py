@@ -89,7 +89,7 @@ def parse_args():
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrivals per second")
     ap.add_argument("--batch-gap-ms", type=float, default=20.0, help="serving: time between a job's batches")
     ap.add_argument("--max-active", type=int, default=64, help="serving: jobs resident at once")
-    ap.add_argument("--workers", type=int, default=8, help="serving: host worker threads of the server")
+    ap.add_argument("--workers", type=int, default=32, help="serving: host worker threads of the server")
     return ap.parse_args()
 
 
@@ -579,6 +579,7 @@ def run_serving(args, w, rank, world, local_rank):
               "config": {"workload": w["desc"], "jobs": len(jobs), "distinct_event_sets": distinct,
                          "rate_per_s": args.rate, "batch_gap_ms": args.batch_gap_ms,
                          "max_active": args.max_active, "workers": args.workers,
+                         "cuda_device_max_connections": os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS"),
                          "l2": "per-job matrices up to 1.25 GB; jobs overlap"},
               "bit_updates_per_s": bit_updates / wall,
               "offered_events_per_s": n_events / max(specs[-1]["arrival"], 1e-9),
@@ -589,7 +590,16 @@ def run_serving(args, w, rank, world, local_rank):
               "plain_one_after_another": {"jobs": len(events), "events_per_s": plain_events / plain_wall,
                                           "bit_updates_per_s": plain_bits / plain_wall,
                                           "identical_results": bool(identical)},
-              "server": st, "failed_jobs": len(bad), "clocks": clocks.summary(),
+              "server": st,
+              "host_ms": {"admit_per_job": st["admit_ns"] / 1e6 / max(st["admitted"], 1),
+                          "copy_in_per_batch": st["copy_ns"] / 1e6 / max(st["batches"], 1),
+                          "schedule_per_batch": st["schedule_ns"] / 1e6 / max(st["batches"], 1),
+                          "results_per_job": st["result_ns"] / 1e6 / max(st["completed"], 1),
+                          "retire_per_job": st["retire_ns"] / 1e6 / max(st["completed"], 1),
+                          "worker_busy_fraction": (st["admit_ns"] + st["copy_ns"] + st["schedule_ns"] +
+                                                   st["result_ns"] + st["retire_ns"]) / 1e9 /
+                                                  (wall * args.workers)},
+              "failed_jobs": len(bad), "clocks": clocks.summary(),
               "e2e": {"value": n_events / wall, "unit": "events/s",
                       "h2d_bytes_per_step": n_events * 16 / len(jobs),
                       "d2h_bytes_per_step": sum(e[0] * 4 + 4 for _, e in jobs) / len(jobs)}}
@@ -1013,6 +1023,11 @@ def run_sweep(args, w, rank, world, local_rank):
 def main():
     args = parse_args()
     w = WORKLOADS[args.workload]
+    if w["kind"] == "serving":
+        # jobs run on two streams each: with the default 8 hardware work queues a
+        # job's short scheduling kernels wait behind other jobs' long updates that
+        # share their queue; 32 is the most a context has (read at its creation)
+        os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -433,6 +433,12 @@ tn_status tn_hash_estimate_noalloc(const uint64_t *P, uint32_t R, uint32_t k, co
  * batch the out-sizes (and the largest out-component) are copied to the
  * caller's host buffers.  Results are exactly those of
  * tn_out_component_sizes_host on the concatenated events.
+ *
+ * Each resident job uses two streams (scheduling, updates).  A process that
+ * serves many jobs at once should raise CUDA_DEVICE_MAX_CONNECTIONS (an
+ * environment variable read when the CUDA context is created) to 32: with the
+ * default 8 hardware work queues, a job's short scheduling kernels queue behind
+ * other jobs' long-running updates that share their hardware queue.
  */
 typedef struct tn_server tn_server;
 
@@ -442,7 +448,7 @@ typedef struct tn_server_options {
     uint32_t window_events; /* plan options of every batch (0 = defaults) */
     uint32_t slab_words;    /* 0 = per job: the widest even slab (at most 16 words)
                                that still gives the job 16 CTAs, at least 2 words */
-    uint32_t workers;       /* host worker threads (0 = 8): admission, copies in,
+    uint32_t workers;       /* host worker threads (0 = 16): admission, copies in,
                                scheduling of batches */
     uint32_t reserved[2];   /* must be zero */
 } tn_server_options;
@@ -463,6 +469,12 @@ typedef struct tn_job_record {
 typedef struct tn_server_stats {
     uint64_t queued, active, admitted, completed;
     uint64_t bytes_in_use, budget, peak_active, peak_bytes;
+    /* host time spent by the workers, summed over them (ns): admitting jobs
+     * (streams, state, buffers), copying batches in, pushing them to the
+     * jobs' online states (validation and scheduling, which wait for the
+     * planner's kernels), enqueueing results, and retiring finished jobs */
+    uint64_t batches;
+    uint64_t admit_ns, copy_ns, schedule_ns, result_ns, retire_ns;
 } tn_server_stats;
 
 #define TN_LAST_BATCH 16u     /* tn_server_push: the job's last batch */

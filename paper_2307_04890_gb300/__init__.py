@@ -82,7 +82,8 @@ class _JobRecord(ctypes.Structure):
 
 class _ServerStats(ctypes.Structure):
     _fields_ = [(name, ctypes.c_uint64) for name in ("queued", "active", "admitted", "completed", "bytes_in_use",
-                                                     "budget", "peak_active", "peak_bytes")]
+                                                     "budget", "peak_active", "peak_bytes", "batches", "admit_ns",
+                                                     "copy_ns", "schedule_ns", "result_ns", "retire_ns")]
 
 
 class _TuneResult(ctypes.Structure):

@@ -29,6 +29,32 @@ void tn_internal_keep_pool(void)
     }
     done[dev] = true;
 }
+cudaError_t tn_internal_stream_wait(cudaStream_t st)
+{
+    struct Cached {
+        int dev = -1;
+        cudaEvent_t ev = nullptr;
+        ~Cached()
+        {
+            if (ev) cudaEventDestroy(ev);
+        }
+    };
+    thread_local Cached c;
+    int dev = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return err;
+    if (c.dev != dev) {
+        if (c.ev) cudaEventDestroy(c.ev);
+        c.ev = nullptr;
+        err = cudaEventCreateWithFlags(&c.ev, cudaEventBlockingSync | cudaEventDisableTiming);
+        if (err != cudaSuccess) return err;
+        c.dev = dev;
+    }
+    err = cudaEventRecord(c.ev, st);
+    if (err != cudaSuccess) return err;
+    return cudaEventSynchronize(c.ev);
+}
+
 cudaError_t tn_internal_allow_max_dyn_smem(const void *kernel)
 {
     int dev = 0, optin = 0;

@@ -25,6 +25,11 @@ void tn_internal_keep_pool(void);
 cudaError_t tn_internal_allow_max_dyn_smem(const void *kernel);
 // Adds `count` to the process-wide kernel launch counter (tn_kernel_launches).
 void tn_internal_count_launches(uint64_t count);
+// Waits on the host for the work enqueued on `stream` so far, sleeping rather
+// than spinning (an event with blocking synchronisation, one per host thread
+// and device): many threads waiting at once (the serving engine's workers)
+// then leave the host cores to the threads that have work.
+cudaError_t tn_internal_stream_wait(cudaStream_t stream);
 
 namespace tn {
 
@@ -252,6 +257,7 @@ struct tn_plan {
     uint32_t *d_aux;      // [aux]        source lists of global PULL ops
     int64_t *d_tbounds;   // [2]          t_first, t_last
     int32_t *d_status;    // [1]          first asynchronous error
+    int status_shared;    // d_status belongs to the owner (tn::plan_use_status), not to the plan
 };
 
 namespace tn {
@@ -272,6 +278,13 @@ tn_status apply_jobs(const tn_plan *const *plans, uint64_t *const *S, const uint
 // tn_online_status.
 constexpr uint32_t kOnlineFlight = 8;
 tn_status online_use_apply_stream(tn_online *online, cudaStream_t apply_stream);
+// Two-stream mode: the device status word every batch's plan records errors
+// in (0 = none), for a caller that copies it out behind the updates.
+const int32_t *online_status_word(const tn_online *online);
+// Points a plan's status word at `status` (owned by the caller, e.g. one word
+// for every batch of an online state, so an error gates the later batches and
+// is read once); the plan's own word is released on `stream`.
+tn_status plan_use_status(tn_plan *plan, int32_t *status, cudaStream_t stream);
 // Reversed copy of an event sequence (Section 3.4): event m-1-e becomes event e,
 // t -> ~t; with `turn` the endpoints are swapped (directed events).  The three
 // arrays come from the stream-ordered allocator; the caller frees them.

@@ -175,6 +175,7 @@ struct tn_online {
     // of applied batches are released once an event behind their update has
     // completed, without waiting for it
     cudaStream_t ast;
+    int32_t *dstatus;  // status word shared by every batch's plan (device)
     tn_plan *flight[tn::kOnlineFlight];
     cudaEvent_t flight_done[tn::kOnlineFlight];
     uint32_t flight_head, flight_count;
@@ -207,9 +208,7 @@ tn_status reap(tn_online *o, bool wait)
             const cudaError_t q = cudaEventQuery(o->flight_done[i]);
             if (q == cudaErrorNotReady) break;
         }
-        int32_t h = 0;
-        if (cudaMemcpy(&h, o->flight[i]->d_status, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) h = TN_ECUDA;
-        if (h != TN_OK && o->error == TN_OK) o->error = h;
+        // the plans share o->dstatus, read once by tn_online_status
         tn_plan_destroy(o->flight[i], o->ast);
         cudaEventDestroy(o->flight_done[i]);
         o->flight_head = (i + 1) % tn::kOnlineFlight;
@@ -221,7 +220,15 @@ tn_status reap(tn_online *o, bool wait)
 // Waits for the last applied batch and folds its status into the sticky error.
 tn_status settle(tn_online *o, cudaStream_t st)
 {
-    if (o->ast) return reap(o, true);
+    if (o->ast) {
+        reap(o, true);
+        int32_t h = 0;
+        cudaError_t err = cudaMemcpyAsync(&h, o->dstatus, sizeof(h), cudaMemcpyDeviceToHost, o->ast);
+        if (err == cudaSuccess) err = tn_internal_stream_wait(o->ast);
+        if (err != cudaSuccess) h = TN_ECUDA;
+        if (h != TN_OK && o->error == TN_OK) o->error = h;
+        return (tn_status)o->error;
+    }
     if (o->inflight) {
         const tn_status rc = tn_plan_status(o->inflight, st);
         tn_plan_destroy(o->inflight, st);
@@ -283,6 +290,11 @@ tn_status apply_ready(tn_online *o, const uint32_t *u, const uint32_t *v, const 
     tn_status rc = tn_plan_create(u, v, t, count, o->n, nullptr, &o->opt, st, &plan);
     if (rc != TN_OK) return rc;
     if (o->ast) {
+        rc = tn::plan_use_status(plan, o->dstatus, st);
+        if (rc != TN_OK) {
+            tn_plan_destroy(plan, st);
+            return rc;
+        }
         // the plan is complete (tn_plan_create returned), so the update may run
         // on the apply stream behind the earlier ones
         if (o->flight_count == tn::kOnlineFlight) {  // room in the ring: wait for the oldest update
@@ -290,7 +302,7 @@ tn_status apply_ready(tn_online *o, const uint32_t *u, const uint32_t *v, const 
             reap(o, false);
         }
         cudaEvent_t done = nullptr;
-        cudaError_t err = cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
+        cudaError_t err = cudaEventCreateWithFlags(&done, cudaEventBlockingSync | cudaEventDisableTiming);
         if (err == cudaSuccess) {
             rc = tn_plan_apply(plan, o->S, o->n, nullptr, nullptr, 0u, o->ast);
             if (rc == TN_OK) err = cudaEventRecord(done, o->ast);
@@ -401,7 +413,7 @@ extern "C" tn_status tn_online_push(tn_online *o, const uint32_t *u, const uint3
         scan_kernel<<<(int)(b < 1216 ? b : 1216), 256, 0, st>>>(u, v, t, m, o->n, o->scan);
         TN_CUDA_TRY(cudaGetLastError());
         TN_CUDA_TRY(cudaMemcpyAsync(&res, o->scan, sizeof(res), cudaMemcpyDeviceToHost, st));
-        TN_CUDA_TRY(cudaStreamSynchronize(st));
+        TN_CUDA_TRY(tn_internal_stream_wait(st));
         if (res.bad & 1ull) return TN_ERANGE;
         if (res.bad & 2ull) return TN_EORDER;
         if (P > 0 ? res.t_first < o->pending_t : (o->has_applied && res.t_first <= o->t_applied)) return TN_EORDER;
@@ -493,9 +505,13 @@ extern "C" tn_status tn_online_grow(tn_online *o, uint32_t n_new, void *stream)
 tn_status tn::online_use_apply_stream(tn_online *o, cudaStream_t apply_stream)
 {
     if (!o || !apply_stream || o->ast || o->batches || o->inflight) return TN_EINVAL;
+    TN_CUDA_TRY(cudaMallocAsync((void **)&o->dstatus, sizeof(int32_t), apply_stream));
+    TN_CUDA_TRY(cudaMemsetAsync(o->dstatus, 0, sizeof(int32_t), apply_stream));
     o->ast = apply_stream;
     return TN_OK;
 }
+
+const int32_t *tn::online_status_word(const tn_online *o) { return o ? o->dstatus : nullptr; }
 
 extern "C" tn_status tn_online_status(tn_online *o, void *stream)
 {
@@ -525,6 +541,7 @@ extern "C" tn_status tn_online_destroy(tn_online *o, void *stream)
     cudaStream_t st = (cudaStream_t)stream;
     if (o->ast) reap(o, true);
     if (o->inflight) tn_plan_destroy(o->inflight, st);
+    if (o->dstatus) cudaFreeAsync(o->dstatus, o->ast);
     cudaFreeAsync(o->S, o->ast ? o->ast : st);
     cudaFreeAsync(o->scan, st);
     if (o->pu) cudaFreeAsync(o->pu, st);

@@ -982,7 +982,7 @@ extern "C" tn_status tn_plan_create(const uint32_t *u, const uint32_t *v, const 
     // the batch's time bounds travel with the first synchronisation
     TN_STEP(cudaMemcpyAsync(&p->t_first, t, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     TN_STEP(cudaMemcpyAsync(&p->t_last, t + (m - 1), sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    TN_STEP(cudaStreamSynchronize(st));
+    TN_STEP(tn_internal_stream_wait(st));
     if (host_counters[0] & 1ull) {
         rc = TN_ERANGE;
         goto done;
@@ -1015,7 +1015,7 @@ extern "C" tn_status tn_plan_create(const uint32_t *u, const uint32_t *v, const 
     window_scan_kernel<<<1, 1024, 0, st>>>(a.wcount, a.nw, base, d_tot);
     TN_STEP(cudaGetLastError());
     TN_STEP(cudaMemcpyAsync(&host_tot, d_tot, sizeof(Totals), cudaMemcpyDeviceToHost, st));
-    TN_STEP(cudaStreamSynchronize(st));
+    TN_STEP(tn_internal_stream_wait(st));
 
     p->items = host_tot.items;
     p->blob8 = host_tot.blob8;
@@ -1035,7 +1035,7 @@ extern "C" tn_status tn_plan_create(const uint32_t *u, const uint32_t *v, const 
     tbounds_kernel<<<1, 1, 0, st>>>(p->t_first, p->t_last, p->d_tbounds);
     TN_STEP(cudaGetLastError());
     // the plan is complete when this call returns, for use on any stream
-    TN_STEP(cudaStreamSynchronize(st));
+    TN_STEP(tn_internal_stream_wait(st));
     goto done;
 
 fail:
@@ -1076,8 +1076,17 @@ extern "C" tn_status tn_plan_destroy(tn_plan *p, void *stream)
     cudaFreeAsync(p->d_items, st);
     cudaFreeAsync(p->d_aux, st);
     cudaFreeAsync(p->d_tbounds, st);
-    cudaFreeAsync(p->d_status, st);
+    if (!p->status_shared) cudaFreeAsync(p->d_status, st);
     free(p);
+    return TN_OK;
+}
+
+tn_status tn::plan_use_status(tn_plan *p, int32_t *status, cudaStream_t st)
+{
+    if (!p || !status) return TN_EINVAL;
+    if (!p->status_shared) TN_CUDA_TRY(cudaFreeAsync(p->d_status, st));
+    p->d_status = status;
+    p->status_shared = 1;
     return TN_OK;
 }
 
@@ -1106,6 +1115,6 @@ extern "C" tn_status tn_plan_status(tn_plan *p, void *stream)
     int32_t h = 0;
     TN_CUDA_TRY(cudaMemcpyAsync(&h, p->d_status, sizeof(h), cudaMemcpyDeviceToHost, st));
     TN_CUDA_TRY(cudaMemsetAsync(p->d_status, 0, sizeof(int32_t), st));
-    TN_CUDA_TRY(cudaStreamSynchronize(st));
+    TN_CUDA_TRY(tn_internal_stream_wait(st));
     return (tn_status)h;
 }

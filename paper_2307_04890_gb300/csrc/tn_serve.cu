@@ -24,6 +24,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -37,7 +38,7 @@
 
 namespace {
 
-constexpr uint32_t kDefaultWorkers = 8;
+constexpr uint32_t kDefaultWorkers = 16;
 constexpr uint64_t kBytesPerBatchEvent = 160;  // copy in 16, held-back group 16, schedule ~128
 
 uint64_t now_ns()
@@ -54,6 +55,20 @@ struct ServeBatch {
     bool last = false;
 };
 
+// The device resources of a resident job, reused by the next job that takes
+// the slot (creating and destroying streams, events and buffers per job would
+// serialise the workers in the driver): a stream for copies and scheduling, a
+// stream for matrix updates, sizes and the copy back, the job's completion
+// event, copy-in buffers, result buffers and the pinned staging of the results.
+struct ServeSlot {
+    cudaStream_t st = nullptr, ast = nullptr;
+    cudaEvent_t done = nullptr;
+    uint32_t *du = nullptr, *dv = nullptr, *d_out = nullptr, *d_am = nullptr;
+    int64_t *dt = nullptr;
+    uint32_t *h_pin = nullptr;
+    uint64_t cap_events = 0, cap_nodes = 0, cap_pin = 0;
+};
+
 struct ServeJob {
     uint64_t id = 0;
     uint32_t n = 0;
@@ -67,12 +82,9 @@ struct ServeJob {
     bool finishing = false;          // results enqueued (or the job failed): retire when done
     uint64_t events = 0;
     // device state, used by one worker at a time: copies in and scheduling on
-    // st, matrix updates, sizes and the copy back on ast
-    cudaStream_t st = nullptr, ast = nullptr;
-    cudaEvent_t done = nullptr;
+    // slot->st, matrix updates, sizes and the copy back on slot->ast
+    ServeSlot *slot = nullptr;
     tn_online *on = nullptr;
-    uint32_t *du = nullptr, *dv = nullptr, *d_out = nullptr, *d_am = nullptr;
-    int64_t *dt = nullptr;
     tn_status status = TN_OK;
     uint64_t t_open = 0, t_admit = 0, t_last_push = 0, t_enqueued = 0, t_done = 0;
 };
@@ -92,9 +104,11 @@ struct tn_server {
     std::condition_variable finished_cv;
     uint64_t in_use = 0;
     uint64_t admitted = 0, completed = 0, peak_active = 0, peak_bytes = 0;
+    std::atomic<uint64_t> batches{0}, admit_ns{0}, copy_ns{0}, schedule_ns{0}, result_ns{0}, retire_ns{0};
     uint64_t starting = 0;  // admissions in progress
     bool stop = false;
     std::vector<std::thread> workers;
+    std::vector<ServeSlot *> slots;  // free slots of finished jobs
 };
 
 namespace {
@@ -120,78 +134,169 @@ uint32_t serve_slab_words(uint32_t n)
     return sw < 2 ? 2u : (uint32_t)sw;
 }
 
-// Streams, online state (two-stream mode), copy-in buffers and result buffers
-// of an admitted job.
+ServeSlot *take_slot(tn_server *s)
+{
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        if (!s->slots.empty()) {
+            ServeSlot *sl = s->slots.back();
+            s->slots.pop_back();
+            return sl;
+        }
+    }
+    ServeSlot *sl = new (std::nothrow) ServeSlot();
+    if (!sl) return nullptr;
+    // scheduling (short kernels the worker waits for) before matrix updates
+    // (long-running CTAs): highest priority for st, lowest for ast
+    int least = 0, greatest = 0;
+    cudaError_t err = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (err == cudaSuccess) err = cudaStreamCreateWithPriority(&sl->st, cudaStreamNonBlocking, greatest);
+    if (err == cudaSuccess) err = cudaStreamCreateWithPriority(&sl->ast, cudaStreamNonBlocking, least);
+    if (err == cudaSuccess) err = cudaEventCreateWithFlags(&sl->done, cudaEventDisableTiming);
+    if (err != cudaSuccess) {
+        tn_internal_set_cuda_error(err);
+        if (sl->done) cudaEventDestroy(sl->done);
+        if (sl->ast) cudaStreamDestroy(sl->ast);
+        if (sl->st) cudaStreamDestroy(sl->st);
+        delete sl;
+        return nullptr;
+    }
+    return sl;
+}
+
+void free_slot(ServeSlot *sl)
+{
+    if (sl->du) cudaFreeAsync(sl->du, sl->st);
+    if (sl->dv) cudaFreeAsync(sl->dv, sl->st);
+    if (sl->dt) cudaFreeAsync(sl->dt, sl->st);
+    if (sl->d_out) cudaFreeAsync(sl->d_out, sl->ast);
+    if (sl->d_am) cudaFreeAsync(sl->d_am, sl->ast);
+    if (sl->st) cudaStreamSynchronize(sl->st);
+    if (sl->ast) cudaStreamSynchronize(sl->ast);
+    if (sl->h_pin) cudaFreeHost(sl->h_pin);
+    if (sl->done) cudaEventDestroy(sl->done);
+    if (sl->ast) cudaStreamDestroy(sl->ast);
+    if (sl->st) cudaStreamDestroy(sl->st);
+    delete sl;
+}
+
+// Buffers of a slot large enough for this job; they only grow.  Device buffers
+// come from the stream-ordered pool on the slot's own streams (a plain free
+// would synchronise the device); the pinned staging is rounded up to a power
+// of two of at least 64 Ki entries, so it rarely grows.
+tn_status fit_slot(ServeSlot *sl, uint64_t max_batch, uint32_t n)
+{
+    const uint64_t mb = max_batch ? max_batch : 1;
+    if (sl->cap_events < mb) {
+        if (sl->du) cudaFreeAsync(sl->du, sl->st);
+        if (sl->dv) cudaFreeAsync(sl->dv, sl->st);
+        if (sl->dt) cudaFreeAsync(sl->dt, sl->st);
+        sl->du = sl->dv = nullptr;
+        sl->dt = nullptr;
+        sl->cap_events = 0;
+        SERVE_TRY(cudaMallocAsync((void **)&sl->du, mb * 4, sl->st));
+        SERVE_TRY(cudaMallocAsync((void **)&sl->dv, mb * 4, sl->st));
+        SERVE_TRY(cudaMallocAsync((void **)&sl->dt, mb * 8, sl->st));
+        sl->cap_events = mb;
+    }
+    if (sl->cap_nodes < n) {
+        if (sl->d_out) cudaFreeAsync(sl->d_out, sl->ast);
+        sl->d_out = nullptr;
+        sl->cap_nodes = 0;
+        if (!sl->d_am) SERVE_TRY(cudaMallocAsync((void **)&sl->d_am, 4, sl->ast));
+        SERVE_TRY(cudaMallocAsync((void **)&sl->d_out, (uint64_t)n * 4, sl->ast));
+        sl->cap_nodes = n;
+    }
+    if (sl->cap_pin < (uint64_t)n + 2) {  // sizes, argmax, status
+        uint64_t c = 1ull << 16;
+        while (c < (uint64_t)n + 2) c *= 2;
+        if (sl->h_pin) cudaFreeHost(sl->h_pin);
+        sl->h_pin = nullptr;
+        sl->cap_pin = 0;
+        SERVE_TRY(cudaHostAlloc((void **)&sl->h_pin, c * 4, cudaHostAllocDefault));
+        sl->cap_pin = c;
+    }
+    return TN_OK;
+}
+
+// Slot (streams, buffers) and online state (two-stream mode) of an admitted job.
 tn_status start_job(tn_server *s, ServeJob *j)
 {
-    SERVE_TRY(cudaStreamCreateWithFlags(&j->st, cudaStreamNonBlocking));
-    SERVE_TRY(cudaStreamCreateWithFlags(&j->ast, cudaStreamNonBlocking));
-    SERVE_TRY(cudaEventCreateWithFlags(&j->done, cudaEventDisableTiming));
-    const uint64_t mb = j->max_batch ? j->max_batch : 1;
-    SERVE_TRY(cudaMallocAsync((void **)&j->du, mb * 4, j->st));
-    SERVE_TRY(cudaMallocAsync((void **)&j->dv, mb * 4, j->st));
-    SERVE_TRY(cudaMallocAsync((void **)&j->dt, mb * 8, j->st));
-    SERVE_TRY(cudaMallocAsync((void **)&j->d_out, (uint64_t)j->n * 4, j->ast));
-    SERVE_TRY(cudaMallocAsync((void **)&j->d_am, 4, j->ast));
+    j->slot = take_slot(s);
+    if (!j->slot) return TN_ECUDA;
+    ServeSlot *sl = j->slot;
+    tn_status rc = fit_slot(sl, j->max_batch, j->n);
+    if (rc != TN_OK) return rc;
     tn_plan_options opt;
     memset(&opt, 0, sizeof(opt));
     opt.window_events = s->opt.window_events;
     opt.slab_words = s->opt.slab_words ? s->opt.slab_words : serve_slab_words(j->n);
-    // a row buffer of 1,280 slots holds a default 640-event window (two rows per
-    // event): small jobs' narrow slabs then need 20-80 KB, so several of their
-    // CTAs share an SM
-    if (!s->opt.window_events && !s->opt.slab_words) opt.smem_rows = 1280;
-    tn_status rc = tn_online_create(j->n, &opt, j->ast, &j->on);
+    rc = tn_online_create(j->n, &opt, sl->ast, &j->on);
     if (rc != TN_OK) return rc;
-    rc = tn::online_use_apply_stream(j->on, j->ast);
+    rc = tn::online_use_apply_stream(j->on, sl->ast);
     if (rc != TN_OK) return rc;
-    // the state's buffers and the copy-in buffers are ready for both streams
-    SERVE_TRY(cudaStreamSynchronize(j->ast));
-    SERVE_TRY(cudaStreamSynchronize(j->st));
+    // the state's and the slot's buffers are ready for both streams
+    SERVE_TRY(tn_internal_stream_wait(sl->ast));
+    SERVE_TRY(tn_internal_stream_wait(sl->st));
     return TN_OK;
 }
 
 // One batch of an admitted job: copy in, push to the online state, and after
 // the last batch the out-sizes and their copy to the caller.
-tn_status serve_batch(ServeJob *j, const ServeBatch &b)
+tn_status serve_batch(tn_server *s, ServeJob *j, const ServeBatch &b)
 {
+    ServeSlot *sl = j->slot;
+    const uint64_t t0 = now_ns();
     if (b.m) {
-        SERVE_TRY(cudaMemcpyAsync(j->du, b.u, b.m * 4, cudaMemcpyHostToDevice, j->st));
-        SERVE_TRY(cudaMemcpyAsync(j->dv, b.v, b.m * 4, cudaMemcpyHostToDevice, j->st));
-        SERVE_TRY(cudaMemcpyAsync(j->dt, b.t, b.m * 8, cudaMemcpyHostToDevice, j->st));
+        SERVE_TRY(cudaMemcpyAsync(sl->du, b.u, b.m * 4, cudaMemcpyHostToDevice, sl->st));
+        SERVE_TRY(cudaMemcpyAsync(sl->dv, b.v, b.m * 4, cudaMemcpyHostToDevice, sl->st));
+        SERVE_TRY(cudaMemcpyAsync(sl->dt, b.t, b.m * 8, cudaMemcpyHostToDevice, sl->st));
     }
-    tn_status rc = tn_online_push(j->on, j->du, j->dv, j->dt, b.m, b.last ? TN_GROUP_END : 0u, j->st);
+    const uint64_t t1 = now_ns();
+    tn_status rc = tn_online_push(j->on, sl->du, sl->dv, sl->dt, b.m, b.last ? TN_GROUP_END : 0u, sl->st);
+    const uint64_t t2 = now_ns();
+    s->copy_ns += t1 - t0;
+    s->schedule_ns += t2 - t1;
+    s->batches++;
     if (rc != TN_OK || !b.last) return rc;
     tn_online_state state;
     rc = tn_online_get_state(j->on, &state);
     if (rc != TN_OK) return rc;
-    rc = tn_out_sizes(state.S, j->n, j->n, j->d_out, nullptr, j->d_am, j->ast);
+    rc = tn_out_sizes(state.S, j->n, j->n, sl->d_out, nullptr, sl->d_am, sl->ast);
     if (rc != TN_OK) return rc;
-    SERVE_TRY(cudaMemcpyAsync(j->h_out, j->d_out, (uint64_t)j->n * 4, cudaMemcpyDeviceToHost, j->ast));
-    if (j->h_argmax) SERVE_TRY(cudaMemcpyAsync(j->h_argmax, j->d_am, 4, cudaMemcpyDeviceToHost, j->ast));
+    // into pinned staging: the copy runs behind the updates without blocking
+    // this worker; the retiring worker hands the results to the caller
+    SERVE_TRY(cudaMemcpyAsync(sl->h_pin, sl->d_out, (uint64_t)j->n * 4, cudaMemcpyDeviceToHost, sl->ast));
+    SERVE_TRY(cudaMemcpyAsync(sl->h_pin + j->n, sl->d_am, 4, cudaMemcpyDeviceToHost, sl->ast));
+    SERVE_TRY(cudaMemcpyAsync(sl->h_pin + j->n + 1, tn::online_status_word(j->on), 4, cudaMemcpyDeviceToHost,
+                              sl->ast));
+    s->result_ns += now_ns() - t2;
     return TN_OK;
 }
 
-void release_job(ServeJob *j)
+// Frees the job's online state (stream-ordered, behind its work) and returns
+// its slot to the pool.
+void release_job(tn_server *s, ServeJob *j)
 {
-    if (j->on) tn_online_destroy(j->on, j->st);  // waits for the updates in flight on ast
-    if (j->du) cudaFreeAsync(j->du, j->st);
-    if (j->dv) cudaFreeAsync(j->dv, j->st);
-    if (j->dt) cudaFreeAsync(j->dt, j->st);
-    if (j->d_out) cudaFreeAsync(j->d_out, j->ast);
-    if (j->d_am) cudaFreeAsync(j->d_am, j->ast);
-    if (j->ast) cudaStreamSynchronize(j->ast);
-    if (j->st) cudaStreamSynchronize(j->st);
-    if (j->done) cudaEventDestroy(j->done);
-    if (j->ast) cudaStreamDestroy(j->ast);
-    if (j->st) cudaStreamDestroy(j->st);
+    if (j->on) tn_online_destroy(j->on, j->slot->st);
+    j->on = nullptr;
+    if (j->slot) {
+        std::lock_guard<std::mutex> lock(s->mu);
+        s->slots.push_back(j->slot);
+    }
+    j->slot = nullptr;
 }
 
 void finish_job(tn_server *s, ServeJob *j)
 {
+    // a device error of an applied batch: the online state's status word, copied
+    // behind the updates with the results (no synchronisation here)
+    if (j->status == TN_OK && j->slot) j->status = (tn_status)(int32_t)j->slot->h_pin[j->n + 1];
+    if (j->status == TN_OK && j->slot) {  // the job's results reached the staging buffer
+        memcpy(j->h_out, j->slot->h_pin, (size_t)j->n * 4);
+        if (j->h_argmax) *j->h_argmax = j->slot->h_pin[j->n];
+    }
     j->t_done = now_ns();
-    // a device error of an applied batch is sticky in the online state
-    if (j->status == TN_OK && j->on) j->status = tn_online_status(j->on, j->ast);
     tn_job_record r;
     memset(&r, 0, sizeof(r));
     r.job_id = j->id;
@@ -203,7 +308,7 @@ void finish_job(tn_server *s, ServeJob *j)
     r.t_done_ns = j->t_done;
     r.t_last_push_ns = j->t_last_push;
     r.t_enqueued_ns = j->t_enqueued;
-    release_job(j);
+    release_job(s, j);
     {
         std::lock_guard<std::mutex> lock(s->mu);
         s->in_use -= j->bytes;
@@ -223,7 +328,10 @@ bool admit_one(tn_server *s)
         const uint64_t resident = s->active.size() + s->starting;
         if (s->queue.empty() || resident >= s->opt.max_active) return false;
         ServeJob *head = s->queue.front();
-        if (s->in_use + head->bytes > s->budget && resident > 0) return false;
+        // bytes stay charged until a retired job's memory is released (a job
+        // larger than the budget was refused at open, so with nothing charged
+        // the head always fits)
+        if (s->in_use + head->bytes > s->budget) return false;
         s->queue.pop_front();
         s->in_use += head->bytes;
         s->admitted++;
@@ -232,6 +340,7 @@ bool admit_one(tn_server *s)
     }
     j->t_admit = now_ns();
     const tn_status rc = start_job(s, j);
+    s->admit_ns += now_ns() - j->t_admit;
     std::lock_guard<std::mutex> lock(s->mu);
     if (rc != TN_OK) j->status = rc;
     s->starting--;
@@ -259,8 +368,8 @@ bool serve_one(tn_server *s)
         }
     }
     if (!j) return false;
-    if (j->status == TN_OK) j->status = serve_batch(j, b);
-    if (b.last && j->done && j->ast) cudaEventRecord(j->done, j->ast);
+    if (j->status == TN_OK) j->status = serve_batch(s, j, b);
+    if (b.last && j->slot) cudaEventRecord(j->slot->done, j->slot->ast);
     std::lock_guard<std::mutex> lock(s->mu);
     j->busy = false;
     if (b.last) {
@@ -279,7 +388,7 @@ bool retire_done(tn_server *s)
         for (size_t i = 0; i < s->active.size();) {
             ServeJob *j = s->active[i];
             const bool ready = j->finishing && !j->busy &&
-                               (!j->done || cudaEventQuery(j->done) != cudaErrorNotReady);
+                               (!j->slot || cudaEventQuery(j->slot->done) != cudaErrorNotReady);
             if (ready) {
                 done.push_back(j);
                 s->open.erase(j->id);
@@ -290,7 +399,9 @@ bool retire_done(tn_server *s)
             }
         }
     }
+    const uint64_t t0 = now_ns();
     for (ServeJob *j : done) finish_job(s, j);
+    if (!done.empty()) s->retire_ns += now_ns() - t0;
     return !done.empty();
 }
 
@@ -484,6 +595,12 @@ extern "C" tn_status tn_server_get_stats(tn_server *s, tn_server_stats *out)
     out->budget = s->budget;
     out->peak_active = s->peak_active;
     out->peak_bytes = s->peak_bytes;
+    out->batches = s->batches;
+    out->admit_ns = s->admit_ns;
+    out->copy_ns = s->copy_ns;
+    out->schedule_ns = s->schedule_ns;
+    out->result_ns = s->result_ns;
+    out->retire_ns = s->retire_ns;
     return TN_OK;
 }
 
@@ -501,9 +618,10 @@ extern "C" tn_status tn_server_destroy(tn_server *s)
     // and waiting): their matrices are released without results
     for (auto &kv : s->open) {
         ServeJob *j = kv.second;
-        release_job(j);
+        release_job(s, j);
         delete j;
     }
+    for (ServeSlot *sl : s->slots) free_slot(sl);
     delete s;
     return TN_OK;
 }
