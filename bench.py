@@ -611,8 +611,9 @@ def run_hashed(args, w, rank, world, local_rank):
     """Network hashing end to end (Section 4): hash tables and super-events, the
     R proxy schedules and the schedule of the sampled exact columns, the R
     proxy matrices and the exact sampled columns in ONE persistent launch
-    (job list: proxies at 32-word slabs, 4 CTAs each, and the 65,536 sampled
-    columns at 16-word slabs, 64 CTAs: 96 CTAs of 12 consumer warps), the fused
+    (job list: proxies at 24-word slabs, 11 CTAs each, and the 65,536 sampled
+    columns at 16-word slabs, 64 CTAs: one wave of 152 CTAs of 12 consumer
+    warps), the fused
     estimate for the sampled sources, their exact out-sizes and the error
     against them.  Beside the step: the same work in separate launches, the
     proxies replayed as a CUDA graph against one launch per proxy (identical
@@ -644,7 +645,7 @@ def run_hashed(args, w, rank, world, local_rank):
     seed = 0  # replica j hashes with splitmix64(seed ^ j): seeds 0..R-1
     ev = lambda: torch.cuda.Event(enable_timing=True)
     # launch shapes of the combined launch (measured against the alternatives: the design doc)
-    popts = dict(slab_words=32, window_events=640, smem_rows=160 * 1024 // (8 * 32))
+    popts = dict(slab_words=24, window_events=480, smem_rows=192 * 1024 // (8 * 24))
     xopts = dict(slab_words=16, window_events=640, smem_rows=0)
     timing = {"combined_ms": [], "estimate_ms": []}
 
