@@ -509,11 +509,18 @@ def run_serving(args, w, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     specs = synth.serving_jobs(args.jobs, rate=args.rate, seed=w["seed"] + 1000 * rank)
     distinct = min(args.distinct_jobs, len(specs))
+    pinned = []  # the events wait in pinned host memory, as a serving front end would hold them
+
+    def pin(a, view):
+        p_ = torch.from_numpy(a.view(view)).pin_memory()
+        pinned.append(p_)
+        return p_.numpy().view(a.dtype)
+
     events = []
     for spec in specs[:distinct]:
         u, v, t = synth.job_events(spec)
         bounds = synth.split_batches(t, 4)
-        events.append((spec["n"], u, v, t, bounds))
+        events.append((spec["n"], pin(u, np.int32), pin(v, np.int32), pin(t, np.int64), bounds))
     jobs = [(spec, events[i % distinct]) for i, spec in enumerate(specs)]
     gap = args.batch_gap_ms * 1e-3
 
@@ -577,6 +584,7 @@ def run_serving(args, w, rank, world, local_rank):
               "steps": len(jobs), "warmup": len(warm), "ms_per_step": wall * 1e3 / len(jobs),
               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
               "config": {"workload": w["desc"], "jobs": len(jobs), "distinct_event_sets": distinct,
+                         "host_events": "pinned",
                          "rate_per_s": args.rate, "batch_gap_ms": args.batch_gap_ms,
                          "max_active": args.max_active, "workers": args.workers,
                          "cuda_device_max_connections": os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS"),

@@ -281,6 +281,11 @@ tn_status online_use_apply_stream(tn_online *online, cudaStream_t apply_stream);
 // Two-stream mode: the device status word every batch's plan records errors
 // in (0 = none), for a caller that copies it out behind the updates.
 const int32_t *online_status_word(const tn_online *online);
+// tn_plan_create without its last host wait: the plan's device buffers are
+// written by work enqueued on `stream`, so a use on another stream must first
+// wait for an event recorded on `stream` after this call.
+tn_status plan_create_ordered(const uint32_t *u, const uint32_t *v, const int64_t *t, uint64_t m, uint32_t n,
+                              const tn_plan_options *opt, cudaStream_t stream, tn_plan **plan_out);
 // Points a plan's status word at `status` (owned by the caller, e.g. one word
 // for every batch of an online state, so an error gates the later batches and
 // is read once); the plan's own word is released on `stream`.

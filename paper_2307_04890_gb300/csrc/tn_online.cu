@@ -287,12 +287,24 @@ tn_status apply_ready(tn_online *o, const uint32_t *u, const uint32_t *v, const 
                       cudaStream_t st)
 {
     tn_plan *plan = nullptr;
-    tn_status rc = tn_plan_create(u, v, t, count, o->n, nullptr, &o->opt, st, &plan);
+    // two-stream mode: the update waits for the plan's last kernels through an
+    // event on the apply stream instead of a host wait
+    tn_status rc = o->ast ? tn::plan_create_ordered(u, v, t, count, o->n, &o->opt, st, &plan)
+                          : tn_plan_create(u, v, t, count, o->n, nullptr, &o->opt, st, &plan);
     if (rc != TN_OK) return rc;
     if (o->ast) {
         rc = tn::plan_use_status(plan, o->dstatus, st);
+        cudaEvent_t planned = nullptr;
+        cudaError_t perr = cudaEventCreateWithFlags(&planned, cudaEventDisableTiming);
+        if (perr == cudaSuccess) perr = cudaEventRecord(planned, st);
+        if (perr == cudaSuccess) perr = cudaStreamWaitEvent(o->ast, planned, 0);
+        if (planned) cudaEventDestroy(planned);  // released once it has completed
+        if (perr != cudaSuccess) {
+            tn_internal_set_cuda_error(perr);
+            rc = TN_ECUDA;
+        }
         if (rc != TN_OK) {
-            tn_plan_destroy(plan, st);
+            tn_plan_destroy(plan, st);  // behind the kernels that write it
             return rc;
         }
         // the plan is complete (tn_plan_create returned), so the update may run

@@ -901,9 +901,11 @@ static cudaError_t alloc_async(T **p, uint64_t count, cudaStream_t st)
 
 using namespace tn;
 
-extern "C" tn_status tn_plan_create(const uint32_t *u, const uint32_t *v, const int64_t *t, uint64_t m,
-                                    uint32_t n, const int64_t *t_after, const tn_plan_options *opt,
-                                    void *stream, tn_plan **plan_out)
+// wait_end: return only once the plan's device buffers are written (else they
+// are written by work enqueued on `stream`, which later users must follow)
+static tn_status plan_create_impl(const uint32_t *u, const uint32_t *v, const int64_t *t, uint64_t m, uint32_t n,
+                                  const int64_t *t_after, const tn_plan_options *opt, void *stream,
+                                  tn_plan **plan_out, bool wait_end)
 {
     if (!plan_out) return TN_EINVAL;
     *plan_out = nullptr;
@@ -1035,7 +1037,7 @@ extern "C" tn_status tn_plan_create(const uint32_t *u, const uint32_t *v, const 
     tbounds_kernel<<<1, 1, 0, st>>>(p->t_first, p->t_last, p->d_tbounds);
     TN_STEP(cudaGetLastError());
     // the plan is complete when this call returns, for use on any stream
-    TN_STEP(tn_internal_stream_wait(st));
+    if (wait_end) TN_STEP(tn_internal_stream_wait(st));
     goto done;
 
 fail:
@@ -1066,6 +1068,19 @@ done:
     *plan_out = p;
     return TN_OK;
 #undef TN_STEP
+}
+
+extern "C" tn_status tn_plan_create(const uint32_t *u, const uint32_t *v, const int64_t *t, uint64_t m,
+                                    uint32_t n, const int64_t *t_after, const tn_plan_options *opt,
+                                    void *stream, tn_plan **plan_out)
+{
+    return plan_create_impl(u, v, t, m, n, t_after, opt, stream, plan_out, true);
+}
+
+tn_status tn::plan_create_ordered(const uint32_t *u, const uint32_t *v, const int64_t *t, uint64_t m, uint32_t n,
+                                  const tn_plan_options *opt, cudaStream_t stream, tn_plan **plan_out)
+{
+    return plan_create_impl(u, v, t, m, n, nullptr, opt, stream, plan_out, false);
 }
 
 extern "C" tn_status tn_plan_destroy(tn_plan *p, void *stream)
