@@ -432,8 +432,8 @@ def run_reference(args, w, rank, world):
               f"columns ({threads} threads, one column slab each); extrapolated linearly to all {n} columns")
     line = {"impl": "reference", "metric": metric, "value": value, "unit": unit, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": w["desc"], "n": n, "m": w["m"]},
+            "scaling": "weak" if w["kind"] == "online" else "strong", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic", "config": {"workload": w["desc"], "n": n, "m": w["m"]},
             "events_per_s": statistics.mean(rates) / n,
             "cpu_baseline": {"value": value, "unit": unit, "cores": threads, "kind": "oracle", "sample": sample,
                              "extrapolated": cols < n, "nproc": os.cpu_count(), "cpu_model": cpu_model()},

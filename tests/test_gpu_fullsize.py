@@ -102,12 +102,17 @@ def test_hashed_n1e6_m1e8_bench_config():
     du, dv, dt = dev(u), dev(v), dev(t, np.int64)
     H, pu, pv = tn.tn_hash_proxy(du, dv, n, k, R, 0)
     P = torch.empty((R, k, tn.tn_row_words(k)), dtype=torch.int64, device="cuda")
-    plans = [tn.Plan(pu[j].contiguous(), pv[j].contiguous(), dt, k) for j in range(R)]
-    tn.tn_plan_apply_batch(plans, [P[j] for j in range(R)], init=True)
     src = dev(src_np)
+    # the launch bench.py times: the 8 proxies (24-word slabs) and the sampled exact
+    # columns (16-word slabs) in one job-list launch, one wave of 152 CTAs
+    plans = [tn.Plan(pu[j].contiguous(), pv[j].contiguous(), dt, k, slab_words=24, window_events=480,
+                     smem_rows=192 * 1024 // (8 * 24)) for j in range(R)]
+    plan_x = tn.Plan(du, dv, dt, n, slab_words=16, window_events=640)
+    Sx = torch.empty((n, tn.tn_row_words(nsrc)), dtype=torch.int64, device="cuda")
+    tn.tn_plan_apply_batch(plans + [plan_x], [P[j] for j in range(R)] + [Sx], ncols=[k] * R + [nsrc], init=True,
+                           srcs=[None] * R + [src])
+    assert all(p.status() == 0 for p in plans + [plan_x])
     est = tn.tn_hash_estimate(P, R, k, H, n, src=src).cpu().numpy().view(np.uint32)
-    plan_x = tn.Plan(du, dv, dt, n)
-    Sx = plan_x.apply(None, ncols=nsrc, src=src, init=True)
     exact = tn.tn_out_sizes(Sx, n, nsrc)[0].cpu().numpy().view(np.uint32)
     Hh = H.cpu().numpy().view(np.uint32)
     Href = oracle.hash_nodes(0, R, k, n)
