@@ -651,3 +651,32 @@ def test_large_groups_scheduled_by_the_whole_cta(n, m, t_range, window, smem_row
         plan.apply(S, init=True)
         assert plan.status() == 0
         assert np.array_equal(host_matrix(S, n), oracle.component_matrix(u, v, t, n)), slab
+
+
+@pytest.mark.parametrize("slab,window", [(64, 3000), (26, 3000), (64, 200)])
+def test_directed_through_wide_slabs_and_the_ring(slab, window):
+    """Directed events (footnote to Section 3.1) with tie groups of about 500
+    events: receivers' PULL runs, senders that also receive read from saved
+    rows; through the per-thread ring (windows of 3,000 events, larger than the
+    buffer) and through records (200), at wide slabs (96 row words: 64 + 32)."""
+    n = 6000
+    u, v, t = synth.uniform_events(n, 40_000, t_range=80, seed=41)
+    du, dv, dt = dev_events(u, v, t)
+    plan = tn.Plan(du, dv, dt, n, directed=True, slab_words=slab, window_events=window)
+    S = plan.apply(None, init=True)
+    assert plan.status() == 0
+    assert np.array_equal(host_matrix(S, n), oracle.component_matrix_directed(u, v, t, n))
+
+
+def test_reversed_stream_through_wide_slabs():
+    """The reversed sequence (Section 3.4: the flipped stream, t -> ~t) of a
+    bursty network through 64-word slabs and the ring equals the oracle's
+    reversed matrix (rows = out-components)."""
+    n = 6000
+    u, v, t = synth.powerlaw_bursty(n, 60_000, seed=43)
+    ru, rv, rt = u[::-1].copy(), v[::-1].copy(), ~t[::-1]
+    du, dv, dt = dev_events(ru, rv, rt)
+    plan = tn.Plan(du, dv, dt, n, slab_words=64, window_events=3000)
+    S = plan.apply(None, init=True)
+    assert plan.status() == 0
+    assert np.array_equal(host_matrix(S, n), oracle.component_matrix_reversed(u, v, t, n))
