@@ -929,13 +929,6 @@ def run_online(args, w, rank, world, local_rank):
         dist.destroy_process_group()
 
 
-def slab_for(n):
-    """Widest even slab (at most 16 words) that still gives 16 CTAs, at least 2 words."""
-    import paper_2307_04890_gb300 as tn
-    sw = min(tn.tn_row_words(n) // 16, 16) & ~1
-    return max(sw, 2)
-
-
 def run_sweep(args, w, rank, world, local_rank):
     """The synthetic experiments of Sections 3.5 and 4.4: ER G(n, 2/n) with an
     independent Poisson process per link, n in {100 .. 10^4}, m = 10^4 .. 10^9.
@@ -961,7 +954,20 @@ def run_sweep(args, w, rank, world, local_rank):
     ev = lambda: torch.cuda.Event(enable_timing=True)
     points = []
     mmax = int(args.sweep_max_m)
+    keys = ("window_events", "slab_words", "smem_rows", "wave_ctas", "resident_words")
+    tuned = {}
     for n in (100, 200, 500, 1000, 2000, 5000, 10000):
+        # launch shapes from the autotuner, once per n, on the first 2e6 events of the
+        # same kind of network (exact matrix; the K proxies of n_s = 0.3 n nodes)
+        k = max(1, int(0.3 * n))
+        us, vs, ts = synth.er_poisson(n, 2_000_000, seed=w["seed"] + 1000 * rank + n)
+        dus, dvs = (torch.from_numpy(a.view(np.int32)).to(dev) for a in (us, vs))
+        dts = torch.from_numpy(ts).to(dev)
+        ex = tn.tn_autotune(dus, dvs, dts, n, sample_events=2_000_000)
+        _, pus, pvs = tn.tn_hash_proxy(dus, dvs, n, k, K, w["seed"])
+        px = tn.tn_autotune(pus[0].contiguous(), pvs[0].contiguous(), dts, k, replicas=K, sample_events=2_000_000)
+        tuned[n] = ({key: ex[key] for key in keys}, {key: px[key] for key in keys})
+        del dus, dvs, dts, pus, pvs
         m = 10_000
         while m <= mmax:
             seed = w["seed"] + 1000 * rank + n
@@ -979,12 +985,12 @@ def run_sweep(args, w, rank, world, local_rank):
                 e = [ev() for _ in range(4)]
                 torch.cuda.synchronize()
                 e[0].record()
-                plan = tn.Plan(du, dv, dt, n, slab_words=slab_for(n))
+                plan = tn.Plan(du, dv, dt, n, **tuned[n][0])
                 plan.apply(S, init=first)
                 e[1].record()
                 e[2].record()
                 H, pu, pv = tn.tn_hash_proxy(du, dv, n, k, K, w["seed"])
-                plans = [tn.Plan(pu[j].contiguous(), pv[j].contiguous(), dt, k, slab_words=slab_for(k))
+                plans = [tn.Plan(pu[j].contiguous(), pv[j].contiguous(), dt, k, **tuned[n][1])
                          for j in range(K)]
                 tn.tn_plan_apply_batch(plans, [P[j] for j in range(K)], init=first)
                 e[3].record()
@@ -1023,7 +1029,9 @@ def run_sweep(args, w, rank, world, local_rank):
               "n_gpus": world, "steps": len(points), "warmup": 0,
               "ms_per_step": float(np.mean([q["exact_ms"] + q["hashed_ms"] for q in points])),
               "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
-              "data": "synthetic", "config": {"workload": w["desc"], "n_s": "0.3 n", "K": K, "chunk_events": chunk},
+              "data": "synthetic", "config": {"workload": w["desc"], "n_s": "0.3 n", "K": K, "chunk_events": chunk,
+                                             "plan_options": {str(n): {"exact": o[0], "proxies": o[1]}
+                                                              for n, o in tuned.items()}},
               "sweep": points}
     if rank == 0:
         print(json.dumps(result), flush=True)
@@ -1098,7 +1106,8 @@ def main():
     tuned = None
     if args.autotune == "on" or (args.autotune == "auto" and w["kind"] == "bursty"):
         tuned = tn.tn_autotune(du, dv, dt, n, sample_events=args.tune_sample, ncols=ncols)
-        opts = {key: tuned[key] for key in ("window_events", "slab_words", "smem_rows")}
+        opts = {key: tuned[key] for key in ("window_events", "slab_words", "smem_rows", "wave_ctas",
+                                             "resident_words")}
 
     def step(record):
         plan = tn.Plan(du, dv, dt, n, **opts)                                            # a1

@@ -207,8 +207,30 @@ typedef struct tn_plan_options {
                                of 16 and the row has at least N such units, else
                                2 words), e.g. one full wave of the GPU's SMs.  N
                                below ceil(row words / slab_words) is raised to it */
-    uint32_t reserved[3];   /* must be zero */
+    uint32_t resident_words;/* 0: the column-slab form above (rows move between HBM and
+                               shared memory).  1 or 2: the resident-slab form for
+                               small networks: each CTA keeps resident_words 64-bit
+                               words of EVERY row (and of the tie groups' saved rows)
+                               in shared memory for the whole batch and reads only the
+                               schedule, so the matrix is read and written once per
+                               application.  Needs (n + saved rows) * 8 *
+                               resident_words bytes of shared memory per CTA:
+                               tn_plan_create returns TN_EINVAL when n is above
+                               tn_resident_max_rows(resident_words) or the tie groups'
+                               saved rows do not fit beside the rows.  slab_words,
+                               smem_rows and wave_ctas must then be 0.  The plan
+                               applies like any other (identity, source columns,
+                               t_last, batches and graphs, mixed with column-slab
+                               plans in one launch); tn_online_create rejects it */
+    uint32_t reserved[2];   /* must be zero */
 } tn_plan_options;
+
+/* Largest node count n whose rows fit the resident-slab form at
+ * `resident_words` (1 or 2) 64-bit words per row, with no saved rows (a
+ * plan whose tie groups need saved rows needs room for them too); 0 for an
+ * unsupported width.  Host-only, no device call besides the first query of the
+ * current device's shared-memory limit. */
+uint32_t tn_resident_max_rows(uint32_t resident_words);
 
 typedef struct tn_plan_stats {
     uint64_t events;     /* m */
@@ -292,15 +314,19 @@ tn_status tn_graph_destroy(tn_graph *graph);
  * ceil(row words / slab) CTAs in waves of (SMs x CTAs per SM); every candidate
  * is timed on the first `sample_events` events (0 = all) over one wave's worth
  * of CTAs -- whole scratch matrices for small n, the first source columns for
- * large n (columns are independent) -- and scored as waves x that time.
- * Candidates: slab 2/4/8/12/16 words (at most the row width), window
- * 320/640/1024 events, row buffer 160 or 80 KB.  Scratch of one timing run is
- * kept under 4 GiB.  The choice is cached per (device, n, replicas,
- * floor(log2 m)) for the life of the process.  Synchronous.
+ * large n (columns are independent) -- and scored as waves x that time plus
+ * replicas x the time tn_plan_create takes on the sample.
+ * Candidates of the column-slab form: slab 2/4/8/12/16/24/32/48/64 words (at
+ * most the row width), window 320/640/1024 events, row buffer 160 or 80 KB
+ * (192 KB above 16 words).  Candidates of the resident-slab form, when the
+ * network's rows fit (tn_resident_max_rows): resident_words 1/2, window
+ * 640/2048 events.  Scratch of one timing run is kept under half of the free
+ * device memory and 64 GiB.  The choice is cached per (device, n, ncols,
+ * replicas, floor(log2 m)) for the life of the process.  Synchronous.
  */
 typedef struct tn_tune_result {
     tn_plan_options best;   /* options to pass to tn_plan_create */
-    float best_ms;          /* its score: waves x timed sample (ms) */
+    float best_ms;          /* its score: waves x timed sample + replicas x plan time (ms) */
     uint32_t tried;         /* candidates timed */
     uint32_t cached;        /* 1 if the result came from the cache */
     uint32_t pad;

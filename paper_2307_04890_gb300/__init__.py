@@ -58,7 +58,7 @@ class TnError(RuntimeError):
 class _Options(ctypes.Structure):
     _fields_ = [("window_events", ctypes.c_uint32), ("slab_words", ctypes.c_uint32),
                 ("smem_rows", ctypes.c_uint32), ("directed", ctypes.c_uint32), ("wave_ctas", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 3)]
+                ("resident_words", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 2)]
 
 
 class _ErrorStats(ctypes.Structure):
@@ -113,6 +113,7 @@ def load_library(path: str | None = None):
         "tn_status_string": ([i32], ctypes.c_char_p),
         "tn_last_cuda_error": ([], ctypes.c_char_p),
         "tn_row_words": ([u64], u64),
+        "tn_resident_max_rows": ([u32], u32),
         "tn_kernel_launches": ([], u64),
         "tn_init_matrix": ([vp, u32, u32, vp, vp], i32),
         "tn_component_matrix": ([vp, vp, vp, u64, u32, vp, vp, u32, vp], i32),
@@ -195,6 +196,11 @@ def _dev(x, dtype_names, what):
 
 def tn_row_words(ncols: int) -> int:
     return int(load_library().tn_row_words(ncols))
+
+
+def tn_resident_max_rows(resident_words: int) -> int:
+    """Largest node count whose rows fit the resident-slab form (no saved rows)."""
+    return int(load_library().tn_resident_max_rows(resident_words))
 
 
 def tn_kernel_launches() -> int:
@@ -344,13 +350,13 @@ def tn_error_stats(est, exact, max_value: int, stream=None) -> dict:
     return {name: getattr(out, name) for name, _ in _ErrorStats._fields_}
 
 
-def _plan_options(window_events=0, slab_words=0, smem_rows=0, directed=False, wave_ctas=0):
-    return _Options(window_events, slab_words, smem_rows, 1 if directed else 0, wave_ctas)
+def _plan_options(window_events=0, slab_words=0, smem_rows=0, directed=False, wave_ctas=0, resident_words=0):
+    return _Options(window_events, slab_words, smem_rows, 1 if directed else 0, wave_ctas, resident_words)
 
 
 def tn_out_component_sizes_host(u, v, t, n: int, **plan_options):
     """Whole exact path from host numpy arrays; returns (sizes uint32[n], argmax).
-    ``plan_options``: window_events, slab_words, smem_rows, directed, wave_ctas."""
+    ``plan_options``: window_events, slab_words, smem_rows, directed, wave_ctas, resident_words."""
     import numpy as np
     lib = load_library()
     u = np.ascontiguousarray(u, dtype=np.uint32)
@@ -384,12 +390,13 @@ class Plan:
     """A validated, scheduled event batch (tn_plan_create / tn_plan_apply)."""
 
     def __init__(self, u, v, t, n: int, t_after=None, window_events: int = 0, slab_words: int = 0,
-                 smem_rows: int = 0, directed: bool = False, wave_ctas: int = 0, stream=None):
+                 smem_rows: int = 0, directed: bool = False, wave_ctas: int = 0, resident_words: int = 0,
+                 stream=None):
         lib = load_library()
         self.m = _events(u, v, t)
         self.n = n
         self.device = u.device
-        opt = _Options(window_events, slab_words, smem_rows, 1 if directed else 0, wave_ctas)
+        opt = _Options(window_events, slab_words, smem_rows, 1 if directed else 0, wave_ctas, resident_words)
         h = ctypes.c_void_p()
         if t_after is not None:
             _dev(t_after, ("int64",), "t_after")
@@ -560,7 +567,8 @@ def tn_autotune(u, v, t, n: int, replicas: int = 1, sample_events: int = 200_000
     _check(lib.tn_autotune(_ptr(u), _ptr(v), _ptr(t), m, n, ncols, replicas, sample_events, _stream(stream),
                            ctypes.byref(res)), "tn_autotune")
     return {"window_events": res.best.window_events, "slab_words": res.best.slab_words,
-            "smem_rows": res.best.smem_rows, "wave_ctas": res.best.wave_ctas, "best_ms": res.best_ms, "tried": res.tried,
+            "smem_rows": res.best.smem_rows, "wave_ctas": res.best.wave_ctas,
+            "resident_words": res.best.resident_words, "best_ms": res.best_ms, "tried": res.tried,
             "cached": bool(res.cached), "sample_events": res.sample_events}
 
 

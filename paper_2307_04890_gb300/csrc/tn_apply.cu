@@ -24,6 +24,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
+
 #include "tn_internal.cuh"
 
 namespace tn {
@@ -53,11 +55,17 @@ struct Job {
     uint32_t cpr;   // 16-byte chunks of a row segment = sw / 2
     uint32_t cta_begin;
     uint32_t dcap;  // row slots of the shared-memory row buffer
+    // resident-slab form (rw > 0): each CTA keeps rw words of every row in shared memory
+    uint32_t rw;     // words of every row per CTA (1, 2 or 4), 0 = column-slab form
+    uint32_t rows;   // rows of the matrix (node count of the plan)
+    uint32_t ntemp;  // saved-row slots of the plan's tie groups
+    uint64_t blob8;  // schedule length in 8-byte units
 };
 
 struct JobList {
     Job job[kMaxJobs];
     uint32_t count;
+    uint32_t smem_bytes;  // dynamic shared memory of the launch
 };
 
 struct StageHdr {
@@ -104,9 +112,24 @@ __device__ inline uint64_t *row_ptr(const Job &J, uint32_t ref, uint64_t col)
 }
 
 __device__ inline void consumers_sync() { asm volatile("bar.sync 1, %0;" ::"r"(consumers()) : "memory"); }
+__device__ inline void consumers_sync(uint32_t count) { asm volatile("bar.sync 1, %0;" ::"r"(count) : "memory"); }
 
 // Barrier of the consumer warps (named barrier 1) that also ORs a predicate
 // across them, so that every consumer takes the same decision to stop.
+__device__ inline bool consumers_sync_or(bool p, uint32_t count)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred ip, op;\n\t"
+        "setp.ne.u32 ip, %1, 0;\n\t"
+        "bar.red.or.pred op, 1, %2, ip;\n\t"
+        "selp.u32 %0, 1, 0, op;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)p), "r"(count)
+        : "memory");
+    return r != 0;
+}
+
 __device__ inline bool consumers_sync_or(bool p)
 {
     uint32_t r;
@@ -434,6 +457,297 @@ __device__ inline void apply_record(const Job &J, const uint32_t *rec, u64x2 *bu
     // no write-back pass: every written row was stored at its last write
 }
 
+// ---------------------------------------------------------------------------
+// resident slab: for a network small enough that rw words of EVERY row fit in
+// shared memory, the CTA loads its slab of the matrix once, applies the whole
+// schedule there and stores it once; only the schedule streams from L2/HBM.
+// The plan holds global tiles only (node-id ops, one level per tile or more;
+// windows of a resident plan are never local records with ops).  The producer
+// warp copies the schedule blob in fixed chunks of kStageBytes into a ring of
+// `nst` stages with cp.async.bulk; consumers walk the item list, wait for the
+// chunks an item covers, apply its ops (independent inside a level) and meet
+// at a named barrier only where a level ends.  A consumer warp releases a
+// chunk (one arrival on its `empty` barrier) once it has started an item past
+// it, so a stage is refilled only when every warp is done with it.
+// Shared memory: barriers | rows[rows] | saved rows[ntemp] | ring.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kChunk8 = kStageBytes / 8;  // 8-byte units per ring stage
+constexpr uint32_t kResidentMaxStages = 8;
+constexpr uint32_t kResidentHead = 2 * kResidentMaxStages * sizeof(uint64_t);  // the ring's barriers
+constexpr uint32_t kResidentMinStages = 2;
+constexpr uint32_t kResidentConsumers = 256;  // consumer threads of a resident CTA (the rest exit)
+
+template <int RW>
+struct alignas(RW == 1 ? 8 : 16) RRow {
+    uint64_t w[RW];
+};
+
+__host__ __device__ inline uint64_t resident_rows_bytes(uint64_t rows, uint64_t temps, uint32_t rw)
+{
+    return ((rows + temps) * 8ull * rw + 127ull) & ~127ull;
+}
+
+template <bool kMax, int RW>
+__device__ inline RRow<RW> rcombine(RRow<RW> a, const RRow<RW> &b)
+{
+#pragma unroll
+    for (int k = 0; k < RW; ++k) a.w[k] = kMax ? max8x8(a.w[k], b.w[k]) : (a.w[k] | b.w[k]);
+    return a;
+}
+
+template <int RW>
+__device__ inline RRow<RW> ld_rrow(const uint64_t *p)
+{
+    RRow<RW> r;
+    if (RW == 1) {
+        asm volatile("ld.global.cg.u64 %0, [%1];" : "=l"(r.w[0]) : "l"(p) : "memory");
+    } else {
+#pragma unroll
+        for (int k = 0; k < RW; k += 2) {
+            const u64x2 x = ld_row16(p + k);
+            r.w[k] = x.x;
+            r.w[k + 1] = x.y;
+        }
+    }
+    return r;
+}
+
+template <int RW>
+__device__ inline void st_rrow(uint64_t *p, const RRow<RW> &r)
+{
+    if (RW == 1) {
+        asm volatile("st.global.u64 [%0], %1;" ::"l"(p), "l"(r.w[0]) : "memory");
+    } else {
+#pragma unroll
+        for (int k = 0; k < RW; k += 2) st_row16(p + k, u64x2{r.w[k], r.w[k + 1]});
+    }
+}
+
+// Rows of the resident slab by 32-bit shared-memory address.
+template <int RW>
+__device__ inline RRow<RW> lds_rrow(uint32_t a)
+{
+    RRow<RW> r;
+    if (RW == 1) {
+        asm volatile("ld.shared.u64 %0, [%1];" : "=l"(r.w[0]) : "r"(a) : "memory");
+    } else {
+#pragma unroll
+        for (int k = 0; k < RW; k += 2)
+            asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(r.w[k]), "=l"(r.w[k + 1]) : "r"(a + 8u * k) : "memory");
+    }
+    return r;
+}
+
+template <int RW>
+__device__ inline void sts_rrow(uint32_t a, const RRow<RW> &r)
+{
+    if (RW == 1) {
+        asm volatile("st.shared.u64 [%0], %1;" ::"r"(a), "l"(r.w[0]) : "memory");
+    } else {
+#pragma unroll
+        for (int k = 0; k < RW; k += 2)
+            asm volatile("st.shared.v2.u64 [%0], {%1, %2};" ::"r"(a + 8u * k), "l"(r.w[k]), "l"(r.w[k + 1]) : "memory");
+    }
+}
+
+__device__ inline uint2 lds_op(uint32_t a)
+{
+    uint2 r;
+    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(r.x), "=r"(r.y) : "r"(a) : "memory");
+    return r;
+}
+
+// One op of a global tile on the resident rows (shared address rb, node ids)
+// and the saved rows (shared address tb, temp ids).
+template <bool kMax, int RW>
+__device__ inline void resident_op(uint2 op, uint32_t rb, uint32_t tb, const uint32_t *aux)
+{
+    constexpr uint32_t kRowB = 8u * RW;
+    const uint32_t kind = op.x >> kKindShift, a = op.x & kIdMask;
+    const uint32_t pa = rb + a * kRowB;
+    if (kind == kEvent) {
+        const uint32_t pb = rb + op.y * kRowB;
+        const RRow<RW> r = rcombine<kMax, RW>(lds_rrow<RW>(pa), lds_rrow<RW>(pb));
+        sts_rrow<RW>(pa, r);
+        sts_rrow<RW>(pb, r);
+    } else if (kind == kOneway) {
+        sts_rrow<RW>(pa, rcombine<kMax, RW>(lds_rrow<RW>(pa), lds_rrow<RW>(rb + op.y * kRowB)));
+    } else if (kind == kCopy) {
+        sts_rrow<RW>(tb + a * kRowB, lds_rrow<RW>(rb + op.y * kRowB));
+    } else {
+        RRow<RW> acc = lds_rrow<RW>(pa);
+        const uint32_t c = __ldg(aux + op.y);
+        for (uint32_t q = 1; q <= c; ++q) {
+            const uint32_t ref = __ldg(aux + op.y + q);
+            acc = rcombine<kMax, RW>(acc, lds_rrow<RW>((ref & kTempRef) ? tb + (ref & ~kTempRef) * kRowB
+                                                                     : rb + ref * kRowB));
+        }
+        sts_rrow<RW>(pa, acc);
+    }
+}
+
+// Lane L of a warp holds item i0 + L of a batch of 32 as (offset, count |
+// flags << 16); the next batch is loaded one batch ahead, so its L2 latency is
+// hidden behind 32 items of work.
+__device__ inline void load_item(const uint4 *items, uint32_t nitems, uint32_t i, uint32_t &off, uint32_t &cf)
+{
+    off = 0;
+    cf = 0;
+    if (i < nitems) {
+        const uint4 it = __ldg(items + i);
+        off = it.x;
+        cf = it.y | (it.z << 16);  // count < 2^16 (at most one stage), flags < 4
+    }
+}
+
+template <bool kMax, int RW>
+__device__ void resident_slab(const Job &J, uint32_t smem_bytes, uint8_t *smem, uint32_t cta)
+{
+    __shared__ int32_t r_gate;
+    using Row = RRow<RW>;
+    // the job's fields in registers (the barriers' memory clobbers would reload them)
+    const uint4 *const items = J.items;
+    const uint32_t nitems = (uint32_t)J.nitems;
+    const uint32_t *const aux = J.aux;
+    const uint2 *const blob = J.blob;
+    const uint64_t blob8 = J.blob8;
+    int32_t *const status = J.status;
+    uint64_t *const S = J.S;
+    const uint64_t ld = J.ld;
+    const uint32_t rows = J.rows;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);
+    uint64_t *empty = full + kResidentMaxStages;
+    Row *R = reinterpret_cast<Row *>(smem + kResidentHead);
+    const uint32_t rb = smem_addr(R), tb = rb + rows * 8u * RW;  // rows, then saved rows
+    const uint32_t ring_off = kResidentHead + (uint32_t)resident_rows_bytes(rows, J.ntemp, RW);
+    uint8_t *ring = smem + ring_off;
+    // a power of two of stages (at least kResidentMinStages by the plan's check)
+    const uint32_t fit = (smem_bytes - ring_off) / kStageBytes;
+    uint32_t nst = kResidentMaxStages;
+    while (nst > fit) nst >>= 1;
+    const uint32_t smask = nst - 1, sshift = __ffs(nst) - 1;
+    const uint64_t w0 = J.w_begin + (uint64_t)cta * RW;
+    const uint32_t nchunks = (uint32_t)((blob8 + kChunk8 - 1) / kChunk8);
+    const uint32_t C = consumers() < kResidentConsumers ? consumers() : kResidentConsumers;
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+    if (threadIdx.x == 0) {
+        r_gate = *(volatile int32_t *)status;  // an earlier error gates this job
+        for (uint32_t s = 0; s < nst; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], C / 32u);
+        }
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (r_gate != 0 || nitems == 0) return;  // no ops: the slab is unchanged
+
+    if (warp == 0) {
+        // ---------------- producer: the blob in fixed chunks ----------------
+        if (lane == 0) {
+            uint32_t c = 0;
+            for (; c < nchunks; ++c) {
+                const uint32_t s = c & smask;
+                if (c >= nst && !mbar_wait_bounded(&empty[s], ((c >> sshift) - 1u) & 1u)) {
+                    record_status(status, TN_ETIMEOUT);
+                    break;
+                }
+                const uint64_t b8 = (uint64_t)c * kChunk8;
+                uint32_t n8 = blob8 - b8 < kChunk8 ? (uint32_t)(blob8 - b8) : kChunk8;
+                n8 = (n8 + 1u) & ~1u;  // whole 16-byte units (the blob has two spare units)
+                mbar_arrive_expect_tx(&full[s], n8 * 8u);
+                bulk_g2s(ring + (size_t)s * kStageBytes, blob + b8, n8 * 8u, &full[s]);
+            }
+            // no bulk copy may still be writing this CTA's shared memory at exit
+            for (uint32_t q = c > nst ? c - nst : 0; q < c; ++q)
+                mbar_wait_bounded(&full[q & smask], (q >> sshift) & 1u);
+        }
+        return;
+    }
+    // ---------------- consumers ----------------
+    const uint32_t ct = threadIdx.x - 32;
+    if (ct >= C) return;  // small levels keep few warps busy: the others leave
+    {
+        uint32_t i = ct;
+        for (; i + 3 * C < rows; i += 4 * C) {
+            Row r[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) r[k] = ld_rrow<RW>(S + (uint64_t)(i + k * C) * ld + w0);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) R[i + k * C] = r[k];
+        }
+        for (; i < rows; i += C) R[i] = ld_rrow<RW>(S + (uint64_t)i * ld + w0);
+    }
+    // op o of the blob, from the stage of its chunk (which has landed)
+    const uint32_t ringa = smem_addr(ring);
+    auto op_at = [&](uint32_t o) -> uint2 {
+        return lds_op(ringa + ((o / kChunk8) & smask) * kStageBytes + (o % kChunk8) * 8u);
+    };
+    bool failed = false;
+    uint32_t waited = 0;    // chunks [0, waited) have landed, as seen by this thread
+    uint32_t released = 0;  // chunks this warp has released
+    uint32_t boff, bcf, noff, ncf;  // this lane's item of the current and of the next batch
+    load_item(items, nitems, lane, boff, bcf);
+    load_item(items, nitems, 32 + lane, noff, ncf);
+    uint32_t off8 = 0, cf = 0;
+    uint2 op0 = make_uint2(0u, 0u);  // this thread's first op of the next item
+    bool have = false;
+    // Prepares item i: releases the chunks before it, waits for the chunks it
+    // covers, and fetches this thread's first op of it.
+    auto prepare = [&](uint32_t i) {
+        const uint32_t k = i & 31u;
+        if (k == 0 && i > 0) {
+            boff = noff;
+            bcf = ncf;
+            load_item(items, nitems, i + 32 + lane, noff, ncf);
+        }
+        off8 = __shfl_sync(0xffffffffu, boff, k);
+        cf = __shfl_sync(0xffffffffu, bcf, k);
+        const uint32_t count = cf & 0xFFFFu;
+        const uint32_t c0 = off8 / kChunk8, c1 = (off8 + count - 1u) / kChunk8;
+        if (released < c0 || waited <= c1) {  // a chunk boundary (one test in the common case)
+            if (released < c0) {  // every lane of the warp is done with these chunks
+                __syncwarp();
+                if (lane == 0)
+                    for (uint32_t q = released; q < c0; ++q) mbar_arrive(&empty[q & smask]);
+                released = c0;
+            }
+            while (waited <= c1 && !failed) {
+                if (mbar_wait_bounded(&full[waited & smask], (waited >> sshift) & 1u)) {
+                    ++waited;
+                } else {
+                    record_status(status, TN_ETIMEOUT);
+                    failed = true;
+                }
+            }
+        }
+        have = !failed && ct < count && !((cf >> 16) & kItemLocal);
+        op0 = op_at(off8 + ct);  // always inside the ring; used only if `have`
+    };
+    consumers_sync(C);
+    prepare(0);
+    uint32_t lev = 0;
+    for (uint32_t i = 0;;) {
+        const uint32_t count = cf & 0xFFFFu, flags = cf >> 16, base8 = off8;
+        if (have) {
+            resident_op<kMax, RW>(op0, rb, tb, aux);
+            for (uint32_t q = ct + C; q < count; q += C) resident_op<kMax, RW>(op_at(base8 + q), rb, tb, aux);
+        }
+        if (++i == nitems) break;
+        prepare(i);  // item info and first op of the next item load before the barrier
+        // the next level reads what this one wrote; every 64th level end also
+        // agrees on stopping (a thread that gave up skips its work until then)
+        if (flags & kItemLevelEnd) {
+            if ((++lev & 63u) == 0) {
+                if (consumers_sync_or(failed, C)) break;
+            } else {
+                consumers_sync(C);
+            }
+        }
+    }
+    if (consumers_sync_or(failed, C)) return;
+    for (uint32_t i = ct; i < rows; i += C) st_rrow<RW>(S + (uint64_t)i * ld + w0, R[i]);
+}
+
 template <bool kMax>
 __global__ void __launch_bounds__(kMaxThreads) stream_kernel(const __grid_constant__ JobList jl)
 {
@@ -447,6 +761,12 @@ __global__ void __launch_bounds__(kMaxThreads) stream_kernel(const __grid_consta
     __shared__ int32_t gate;
 
     const Job &J = jl.job[find_job(jl, blockIdx.x)];
+    if (J.rw) {
+        const uint32_t cta = blockIdx.x - J.cta_begin;
+        if (J.rw == 1) resident_slab<kMax, 1>(J, jl.smem_bytes, smem, cta);
+        else resident_slab<kMax, 2>(J, jl.smem_bytes, smem, cta);
+        return;
+    }
     const uint64_t w0 = J.w_begin + (uint64_t)(blockIdx.x - J.cta_begin) * J.sw;
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
     if (threadIdx.x == 0) {
@@ -655,6 +975,57 @@ static int split_slabs(uint64_t ld, uint32_t sw, uint32_t wave, SlabSplit out[2]
     return k;
 }
 
+// Dynamic shared memory the streaming kernel can use on the current device
+// (the opt-in maximum minus its static shared memory), cached per device.
+static uint32_t stream_smem_limit()
+{
+    static std::mutex mu;
+    static uint32_t cached[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!cached[dev]) {
+        int optin = 0;
+        cudaFuncAttributes fa;
+        if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+            cudaFuncGetAttributes(&fa, (const void *)stream_kernel<false>) != cudaSuccess)
+            return 0;
+        cached[dev] = (uint32_t)(optin - (int)fa.sharedSizeBytes);
+    }
+    return cached[dev];
+}
+
+static int multiprocessors()
+{
+    static std::mutex mu;
+    static int cached[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!cached[dev] && cudaDeviceGetAttribute(&cached[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        cached[dev] = 0;
+    return cached[dev] > 0 ? cached[dev] : 1;
+}
+
+// dynamic shared memory of a CTA that leaves room for a second one on its SM
+constexpr uint64_t kHalfSmSmem = 112 * 1024;
+
+bool resident_fits(uint64_t rows, uint64_t temps, uint32_t words)
+{
+    if (words != 1 && words != 2) return false;
+    return kResidentHead + resident_rows_bytes(rows, temps, words) + (uint64_t)kResidentMinStages * kStageBytes <=
+           stream_smem_limit();
+}
+
+uint32_t resident_max_rows(uint32_t words)
+{
+    if (words != 1 && words != 2) return 0;
+    const uint64_t lim = stream_smem_limit();
+    const uint64_t fixed = kResidentHead + (uint64_t)kResidentMinStages * kStageBytes;
+    if (lim <= fixed) return 0;
+    return (uint32_t)(((lim - fixed) & ~127ull) / (8ull * words));
+}
+
 static int grid_for(uint64_t work)
 {
     uint64_t g = (work + 255) / 256;
@@ -674,6 +1045,10 @@ tn_status apply_jobs(const tn_plan *const *plans, uint64_t *const *S, const uint
         if ((flags & TN_INIT_IDENTITY) && !src[i] && ncols[i] != p->n) return TN_EINVAL;
     }
     const size_t smem_base = (size_t)kStages * kStageBytes + 2 * kStages * sizeof(uint64_t) + kStages * sizeof(StageHdr);
+    const size_t smem_limit = stream_smem_limit();
+    if ((flags & kApplyMax) || !smem_limit)
+        for (uint32_t i = 0; i < count; ++i)
+            if (plans[i]->resident) return TN_EINVAL;
     uint64_t *tmps[kMaxPlans];
     for (uint32_t base = 0; base < count; base += kMaxPlans) {
         const uint32_t nj = count - base < (uint32_t)kMaxPlans ? count - base : (uint32_t)kMaxPlans;
@@ -687,6 +1062,7 @@ tn_status apply_jobs(const tn_plan *const *plans, uint64_t *const *S, const uint
             const tn_plan *p = plans[i];
             const uint64_t ld = tn_row_words(ncols[i]);
             tmps[j] = nullptr;
+            if (p->resident) continue;  // second pass below
             if (t_last && t_last[i]) {
                 tn_internal_count_launches(1);
                 order_gate_kernel<<<1, 1, 0, st>>>(p->d_tbounds, t_last[i], p->d_status);
@@ -726,6 +1102,76 @@ tn_status apply_jobs(const tn_plan *const *plans, uint64_t *const *S, const uint
                 ctas += sp[k].ctas;
             }
         }
+        // resident-slab jobs after the column-slab ones: their CTAs are short,
+        // and the long column-slab CTAs are dispatched first.  Their schedule
+        // ring has 8 stages (one CTA of 12 consumer warps per SM) while the
+        // resident CTAs fit one wave; beyond that 4, or 2 if only that lets two
+        // CTAs share an SM
+        uint64_t res_ctas = 0, rb_max = 0;
+        for (uint32_t j = 0; j < nj; ++j) {
+            const tn_plan *p = plans[base + j];
+            if (!p->resident) continue;
+            res_ctas += ((ncols[base + j] + 63) / 64 + p->resident - 1) / p->resident;
+            const uint64_t rb = kResidentHead + resident_rows_bytes(p->n, p->temps, p->resident);
+            if (rb > rb_max) rb_max = rb;
+        }
+        uint64_t stages = kResidentMaxStages;
+        if (res_ctas > (uint64_t)multiprocessors()) {
+            stages = 4;
+            if (smem <= kHalfSmSmem && rb_max + 4ull * kStageBytes > kHalfSmSmem &&
+                rb_max + 2ull * kStageBytes <= kHalfSmSmem)
+                stages = 2;
+        }
+        for (uint32_t j = 0; j < nj; ++j) {
+            const uint32_t i = base + j;
+            const tn_plan *p = plans[i];
+            if (!p->resident) continue;
+            const uint64_t ld = tn_row_words(ncols[i]);
+            if (t_last && t_last[i]) {
+                tn_internal_count_launches(1);
+                order_gate_kernel<<<1, 1, 0, st>>>(p->d_tbounds, t_last[i], p->d_status);
+            }
+            if (flags & TN_INIT_IDENTITY) {
+                if (!src[i]) {
+                    tn_internal_count_launches(1);
+                    init_identity_kernel<<<grid_for(p->n * 32ull), 256, 0, st>>>(S[i], p->n, ld, p->d_status);
+                } else {
+                    tn_internal_count_launches(1);
+                    zero_kernel<<<grid_for(p->n * ld / 2), 256, 0, st>>>(S[i], (uint64_t)p->n * ld, p->d_status);
+                    tn_internal_count_launches(1);
+                    init_sources_kernel<<<grid_for(ncols[i]), 256, 0, st>>>(S[i], ld, src[i], ncols[i], p->n,
+                                                                            p->d_status);
+                }
+            }
+            // words holding columns (the rest of the row is zero padding and stays so)
+            const uint64_t used = (ncols[i] + 63) / 64;
+            const uint32_t rw = p->resident;
+            const uint64_t rb = kResidentHead + resident_rows_bytes(p->n, p->temps, rw);
+            uint64_t need = rb + stages * kStageBytes;
+            if (need > smem_limit) need = smem_limit;
+            if (rb + (uint64_t)kResidentMinStages * kStageBytes > smem_limit) return TN_EINVAL;
+            if (need > smem) smem = need;
+            Job &J = jl.job[jl.count++];
+            J.blob = p->d_blob;
+            J.items = p->d_items;
+            J.aux = p->d_aux;
+            J.nitems = p->items;
+            J.S = S[i];
+            J.ld = ld;
+            J.tmp = nullptr;
+            J.status = p->d_status;
+            J.w_begin = 0;
+            J.sw = rw;
+            J.cpr = 0;
+            J.dcap = 0;
+            J.rw = rw;
+            J.rows = p->n;
+            J.ntemp = (uint32_t)p->temps;
+            J.blob8 = p->blob8;
+            J.cta_begin = ctas;
+            ctas += (uint32_t)((used + rw - 1) / rw);
+        }
+        jl.smem_bytes = (uint32_t)smem;
         TN_CUDA_TRY(cudaGetLastError());
         if (ctas) {
             tn_internal_count_launches(1);
@@ -929,3 +1375,5 @@ extern "C" tn_status tn_selftest_wait_timeout(void *stream)
     TN_CUDA_TRY(cudaStreamSynchronize(st));
     return (tn_status)h;
 }
+
+extern "C" uint32_t tn_resident_max_rows(uint32_t resident_words) { return tn::resident_max_rows(resident_words); }

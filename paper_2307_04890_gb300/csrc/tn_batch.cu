@@ -7,16 +7,18 @@
 // launch) is captured once into a CUDA graph and replayed with one launch.
 //
 // The autotuner picks the plan options that decide the launch shape -- slab
-// width (columns per CTA, hence the CTA count), scheduling-window depth, and
-// the size of the shared-memory row buffer (hence CTAs per SM) -- by timing
-// the candidates on a prefix of the events, for a batch of `replicas`
-// networks of the same size, and caches the choice per (device, n, replicas,
-// log2 m).
+// width (columns per CTA, hence the CTA count), scheduling-window depth, the
+// size of the shared-memory row buffer (hence CTAs per SM), or the
+// resident-slab form for small networks -- by timing the candidates (their
+// schedule and their application) on a prefix of the events, for a batch of
+// `replicas` networks of the same size, and caches the choice per (device, n,
+// ncols, replicas, log2 m).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
 
+#include <chrono>
 #include <map>
 #include <mutex>
 #include <new>
@@ -136,13 +138,26 @@ tn_status time_apply(tn_plan *plan, uint64_t *const *mats, uint32_t count, uint3
     return rc;
 }
 
+// tn_plan_create on the sample, with its wall time (the planner synchronises
+// with the host, so this is its whole cost).
+tn_status timed_plan(const uint32_t *u, const uint32_t *v, const int64_t *t, uint64_t m, uint32_t n,
+                     const tn_plan_options *opt, cudaStream_t st, tn_plan **plan, float *ms)
+{
+    TN_CUDA_TRY(cudaStreamSynchronize(st));
+    const auto t0 = std::chrono::steady_clock::now();
+    const tn_status rc = tn_plan_create(u, v, t, m, n, nullptr, opt, st, plan);
+    *ms = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return rc;
+}
+
 }  // namespace
 
 // The full problem (replicas x ceil(row words / slab) CTAs) runs in waves of
 // SMs x CTAs-per-SM; every candidate is timed on one wave's worth of CTAs --
 // whole matrices for small networks, a subset of source columns for large ones
 // (columns are independent, so a CTA's work does not depend on the others) --
-// and scored as waves x that time.
+// and scored as waves x that time plus replicas x the schedule's build time
+// on the sample (each application of a plan is preceded by building it).
 extern "C" tn_status tn_autotune(const uint32_t *u, const uint32_t *v, const int64_t *t, uint64_t m, uint32_t n,
                                  uint32_t ncols_full, uint32_t replicas, uint64_t sample_events, void *stream,
                                  tn_tune_result *out)
@@ -232,7 +247,8 @@ extern "C" tn_status tn_autotune(const uint32_t *u, const uint32_t *v, const int
                 opt.slab_words = sw;
                 opt.smem_rows = (half ? 80u : (sw <= 16 ? 160u : 192u)) * 1024u / (8u * sw);
                 tn_plan *plan = nullptr;
-                rc = tn_plan_create(u, v, t, msample, n, nullptr, &opt, st, &plan);
+                float pms = 0.f;
+                rc = timed_plan(u, v, t, msample, n, &opt, st, &plan, &pms);
                 if (rc != TN_OK) break;
                 float tms = INFINITY;
                 rc = time_apply(plan, mats.data(), reps, ncols, src, st, &tms);
@@ -240,7 +256,7 @@ extern "C" tn_status tn_autotune(const uint32_t *u, const uint32_t *v, const int
                 tn_plan_destroy(plan, st);
                 if (rc != TN_OK) break;
                 out->tried++;
-                const float score = tms * (float)waves;
+                const float score = tms * (float)waves + pms * (float)replicas;
                 if (score < best) {
                     best = score;
                     out->best = opt;
@@ -250,6 +266,72 @@ extern "C" tn_status tn_autotune(const uint32_t *u, const uint32_t *v, const int
             for (uint64_t *p : mats)
                 if (p) cudaFreeAsync(p, st);
         }
+    }
+    // the resident-slab form, for networks whose rows fit shared memory: one
+    // CTA per resident_words words of the row, one CTA per SM beyond a wave
+    // unless two fit (the launch's rule); a plan whose saved rows do not fit
+    // is skipped
+    const uint32_t rws[] = {1, 2};
+    const uint64_t used_words = (ncols_full + 63) / 64;
+    for (uint32_t rw : rws) {
+        if (rc != TN_OK || n > tn::resident_max_rows(rw)) continue;
+        const uint64_t per_rep = (used_words + rw - 1) / rw;
+        const uint64_t total = per_rep * replicas;
+        const uint64_t rb = 128 + (((uint64_t)n * 8 * rw + 127) & ~127ull);
+        const uint64_t occ = (total > (uint64_t)nsm && rb + 2ull * 16384 <= 112ull * 1024) ? 2 : 1;
+        const uint64_t slots = (uint64_t)nsm * occ;
+        const uint64_t waves = (total + slots - 1) / slots;
+        uint32_t reps = 1, ncols = ncols_full;
+        const uint32_t *src = ncols_full < n ? ids : nullptr;
+        if (per_rep >= slots) {
+            const uint64_t c = slots * rw * 64;
+            if (c < ncols_full) {
+                ncols = (uint32_t)c;
+                src = ids;
+            }
+        } else {
+            reps = (uint32_t)((slots + per_rep - 1) / per_rep);
+            if (reps > replicas) reps = replicas;
+            while (reps > 1 && (uint64_t)reps * n * ld * 8 > kTuneBytesLimit) --reps;
+        }
+        if (src && ncols > max_cols) continue;
+        std::vector<uint64_t *> mats(reps, nullptr);
+        const uint64_t mbytes = (uint64_t)n * tn_row_words(ncols) * 8;
+        for (uint32_t r = 0; r < reps && rc == TN_OK; ++r) {
+            const cudaError_t e = cudaMallocAsync((void **)&mats[r], mbytes, st);
+            if (e != cudaSuccess) {
+                tn_internal_set_cuda_error(e);
+                rc = e == cudaErrorMemoryAllocation ? TN_ENOMEM : TN_ECUDA;
+            }
+        }
+        const uint32_t rwindows[] = {640, 2048};
+        for (uint32_t win : rwindows) {
+            if (rc != TN_OK) break;
+            tn_plan_options opt;
+            memset(&opt, 0, sizeof(opt));
+            opt.window_events = win;
+            opt.resident_words = rw;
+            tn_plan *plan = nullptr;
+            float pms = 0.f;
+            const tn_status pc = timed_plan(u, v, t, msample, n, &opt, st, &plan, &pms);
+            if (pc == TN_EINVAL) continue;  // saved rows do not fit beside the rows
+            rc = pc;
+            if (rc != TN_OK) break;
+            float tms = INFINITY;
+            rc = time_apply(plan, mats.data(), reps, ncols, src, st, &tms);
+            if (rc == TN_OK) rc = tn_plan_status(plan, st);
+            tn_plan_destroy(plan, st);
+            if (rc != TN_OK) break;
+            out->tried++;
+            const float score = tms * (float)waves + pms * (float)replicas;
+            if (score < best) {
+                best = score;
+                out->best = opt;
+                out->best_ms = score;
+            }
+        }
+        for (uint64_t *p : mats)
+            if (p) cudaFreeAsync(p, st);
     }
     cudaFreeAsync(ids, st);
     if (rc != TN_OK) return rc;

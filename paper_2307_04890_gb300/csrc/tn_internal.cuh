@@ -252,6 +252,7 @@ struct tn_plan {
     uint32_t slab_words;  // 64-bit words of every row owned by one CTA (the widest, with wave_ctas)
     uint32_t wave_ctas;   // 0, or the number of CTAs one matrix is spread over
     uint32_t dcap;        // row slots of the kernel's shared-memory row buffer
+    uint32_t resident;    // 0, or 64-bit words of every row one CTA keeps in shared memory
     uint2 *d_blob;        // [blob8 + 2]  item payloads (8-byte units)
     uint4 *d_items;       // [items]      work items in execution order
     uint32_t *d_aux;      // [aux]        source lists of global PULL ops
@@ -261,6 +262,12 @@ struct tn_plan {
 };
 
 namespace tn {
+// Resident-slab form (tn_plan_options.resident_words): whether a network of
+// `rows` rows and `temps` saved-row slots fits one CTA's shared memory at
+// `words` 64-bit words per row, beside the smallest schedule ring; and the
+// largest row count that fits with no saved rows (0 for an unsupported width).
+bool resident_fits(uint64_t rows, uint64_t temps, uint32_t words);
+uint32_t resident_max_rows(uint32_t words);
 // Internal apply flag: combine rows by byte-wise maximum (HyperLogLog
 // registers) instead of OR; no initialisation.
 constexpr uint32_t kApplyMax = 1u << 16;

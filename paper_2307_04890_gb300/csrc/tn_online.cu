@@ -363,9 +363,9 @@ extern "C" tn_status tn_online_create(uint32_t n, const tn_plan_options *opt, vo
     *out = nullptr;
     if (n == 0 || n >= (1u << 30)) return TN_EINVAL;
     if (opt) {
-        for (int i = 0; i < 3; ++i)
+        for (int i = 0; i < 2; ++i)
             if (opt->reserved[i]) return TN_EINVAL;
-        if (opt->directed > 1) return TN_EINVAL;
+        if (opt->directed > 1 || opt->resident_words) return TN_EINVAL;
         const uint32_t sw = opt->slab_words;
         if (sw && (sw < 2 || sw > tn::kMaxSlabWords || (sw & 1u))) return TN_EINVAL;
     }

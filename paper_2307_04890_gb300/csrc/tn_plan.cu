@@ -910,18 +910,28 @@ static tn_status plan_create_impl(const uint32_t *u, const uint32_t *v, const in
     if (!plan_out) return TN_EINVAL;
     *plan_out = nullptr;
     if (!u || !v || !t || m == 0 || n == 0 || n >= (1u << 30) || m >= (1ull << 30)) return TN_EINVAL;
-    uint32_t sw = kDefaultSlab, window = kDefaultWindow, rows = 0, wave = 0;
+    uint32_t sw = kDefaultSlab, window = kDefaultWindow, rows = 0, wave = 0, resident = 0;
     if (opt) {
-        for (int i = 0; i < 3; ++i)
+        for (int i = 0; i < 2; ++i)
             if (opt->reserved[i]) return TN_EINVAL;
         if (opt->directed > 1) return TN_EINVAL;
         if (opt->slab_words) sw = opt->slab_words;
         if (opt->window_events) window = opt->window_events;
         rows = opt->smem_rows;
         wave = opt->wave_ctas;
+        resident = opt->resident_words;
     }
     if (sw < 2 || sw > kMaxSlabWords || (sw & 1u)) return TN_EINVAL;  // even: whole 16-byte chunks
     if (window < 32) window = 32;
+    if (resident) {
+        // the resident-slab form keeps every row in shared memory: no row
+        // buffer, and every window becomes level-ordered tiles of node-id ops
+        // (a one-slot buffer holds no window that has an op)
+        if ((resident != 1 && resident != 2) || opt->slab_words || opt->smem_rows || wave)
+            return TN_EINVAL;
+        if (n > resident_max_rows(resident)) return TN_EINVAL;
+        rows = 1;
+    }
     if (rows == 0) rows = (sw <= 16 ? kRowBufferBytes : kRowBufferWide) / (sw * 8);
     if (rows > kLocalSlotLimit) rows = kLocalSlotLimit;
     if ((uint64_t)rows * sw * 8 > kRowBufferWide) return TN_EINVAL;  // row buffer must fit the kernel's shared memory
@@ -952,6 +962,7 @@ static tn_status plan_create_impl(const uint32_t *u, const uint32_t *v, const in
     p->slab_words = sw;
     p->wave_ctas = wave;
     p->dcap = rows;
+    p->resident = resident;
 
     tn_status rc = TN_OK;
     unsigned long long host_counters[4] = {0, 0, 0, 0};
@@ -1026,6 +1037,10 @@ static tn_status plan_create_impl(const uint32_t *u, const uint32_t *v, const in
     p->levels = host_tot.levels;
     p->ops = host_tot.ops;
     p->local_windows = host_tot.local;
+    if (resident && !resident_fits(n, p->temps, resident)) {  // saved rows of the tie groups do not fit
+        rc = TN_EINVAL;
+        goto done;
+    }
     TN_STEP(alloc_async(&p->d_blob, p->blob8 + 2, st));  // a global tile may read one op past its end
     TN_STEP(alloc_async(&p->d_items, p->items > 0 ? p->items : 1, st));
     TN_STEP(alloc_async(&p->d_aux, p->aux > 0 ? p->aux : 1, st));

@@ -90,11 +90,16 @@ def test_autotune_keeps_results(n, m, replicas):
     du, dv, dt = dev(u), dev(v), dev(t, np.int64)
     res = tn.tn_autotune(du, dv, dt, n, replicas=replicas, sample_events=50_000)
     assert res["tried"] > 0 and not res["cached"]
-    assert res["slab_words"] in (2, 4, 8, 12, 16) and res["window_events"] in (320, 640, 1024)
+    if res["resident_words"]:  # the resident-slab form: only for networks whose rows fit
+        assert res["resident_words"] in (1, 2) and n <= tn.tn_resident_max_rows(res["resident_words"])
+        assert res["window_events"] in (640, 2048) and res["slab_words"] == 0 and res["smem_rows"] == 0
+    else:
+        assert res["slab_words"] in (2, 4, 8, 12, 16, 24, 32, 48, 64) and res["window_events"] in (320, 640, 1024)
     again = tn.tn_autotune(du, dv, dt, n, replicas=replicas, sample_events=50_000)
     assert again["cached"] and again["slab_words"] == res["slab_words"]
+    assert again["resident_words"] == res["resident_words"]
     tuned = tn.Plan(du, dv, dt, n, window_events=res["window_events"], slab_words=res["slab_words"],
-                    smem_rows=res["smem_rows"])
+                    smem_rows=res["smem_rows"], resident_words=res["resident_words"])
     plain = tn.Plan(du, dv, dt, n)
     a = tuned.apply(None, init=True)
     b = plain.apply(None, init=True)

@@ -95,3 +95,21 @@ def test_growth_and_online_reject_bad_arguments_before_any_device_call(lib_path)
     assert lib.tn_online_grow(None, 10, None) == tn.TN_EINVAL
     assert lib.tn_online_status(None, None) == tn.TN_EINVAL
     assert lib.tn_online_destroy(None, None) == tn.TN_EINVAL
+
+
+def test_resident_option_checked_before_any_device_call(lib_path):
+    """The resident-slab option is validated on the host: an unsupported width,
+    or one combined with the column-slab options, returns TN_EINVAL, and online
+    states do not take it."""
+    lib = tn.load_library()
+    vp = ctypes.c_void_p
+    fake = vp(0x1000)  # never dereferenced
+    assert tn.tn_resident_max_rows(3) == 0 and tn.tn_resident_max_rows(4) == 0 and tn.tn_resident_max_rows(0) == 0
+    h = vp()
+    for kw in (dict(resident_words=3), dict(resident_words=4), dict(resident_words=8), dict(resident_words=1, slab_words=16),
+               dict(resident_words=2, smem_rows=64), dict(resident_words=1, wave_ctas=152)):
+        opt = tn._plan_options(**kw)
+        assert lib.tn_plan_create(fake, fake, fake, 10, 100, None, ctypes.byref(opt), None,
+                                  ctypes.byref(h)) == tn.TN_EINVAL, kw
+    opt = tn._plan_options(resident_words=1)
+    assert lib.tn_online_create(100, ctypes.byref(opt), None, ctypes.byref(h)) == tn.TN_EINVAL
