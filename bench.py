@@ -54,6 +54,9 @@ WORKLOADS = {
                           kind="scaled", n=40_000, m=2_000_000, seed=3, ncols=123 * 64 * 64, slab=64),
     "uniform-small": dict(desc="uniform pairs n=1000 m=20000, t uniform in [0,1e4)", kind="uniform",
                           n=1000, m=20_000, seed=1, t_range=10_000),
+    "er-small": dict(desc="ER G(n, 2/n) with Poisson link activity, n=10000 m=10000000 (the paper's largest "
+                          "synthetic n; autotuned: the resident-slab form)", kind="er", n=10_000, m=10_000_000,
+                     seed=7),
     "bursty": dict(desc="power-law bursty n=500000 m=100000000 (degree exponent 2.5, Pareto(1.5, 60 s) gaps, "
                         "integer seconds: large tie groups)", kind="bursty", n=500_000, m=100_000_000, seed=3),
     "hashed": dict(desc="hashed estimate n=1000000 m=100000000 activity-driven, k=16384, R=8, 65536 sampled sources",
@@ -77,11 +80,13 @@ def parse_args():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="bursty")
     ap.add_argument("--window", type=int, default=0, help="events per scheduling window (0 = library default)")
     ap.add_argument("--slab", type=int, default=0, help="row words per CTA (0 = library default)")
+    ap.add_argument("--resident", type=int, default=0,
+                    help="resident-slab form with this many row words per CTA (1 or 2; 0 = column slabs)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--autotune", choices=["auto", "on", "off"], default="auto",
-                    help="pick plan options with tn_autotune before timing (auto: on for bursty and hashed)")
+                    help="pick plan options with tn_autotune before timing (auto: on for bursty and er-small)")
     ap.add_argument("--tune-sample", type=int, default=2_000_000, help="events the autotuner times")
     ap.add_argument("--sweep-max-m", type=float, default=1e9, help="er-sweep: largest number of events")
     ap.add_argument("--jobs", type=int, default=2000, help="serving: number of jobs")
@@ -100,6 +105,8 @@ def make_events(w, rank=0):
         return synth.activity_driven(w["n"], w["m"], seed=seed)
     if w["kind"] == "bursty":
         return synth.powerlaw_bursty(w["n"], w["m"], seed=seed)
+    if w["kind"] == "er":
+        return synth.er_poisson(w["n"], w["m"], seed=seed)
     return synth.uniform_events(w["n"], w["m"], t_range=w["t_range"], seed=seed)
 
 
@@ -1102,9 +1109,9 @@ def main():
     stream = torch.cuda.current_stream(dev)
 
     k1_events = []
-    opts = dict(window_events=args.window, slab_words=args.slab, smem_rows=0)
+    opts = dict(window_events=args.window, slab_words=args.slab, smem_rows=0, resident_words=args.resident)
     tuned = None
-    if args.autotune == "on" or (args.autotune == "auto" and w["kind"] == "bursty"):
+    if args.autotune == "on" or (args.autotune == "auto" and w["kind"] in ("bursty", "er")):
         tuned = tn.tn_autotune(du, dv, dt, n, sample_events=args.tune_sample, ncols=ncols)
         opts = {key: tuned[key] for key in ("window_events", "slab_words", "smem_rows", "wave_ctas",
                                              "resident_words")}
@@ -1152,18 +1159,34 @@ def main():
 
     # roofline of the dominant kernel (the column-slab stream of this rank)
     words = (ncols + 63) // 64
-    alg_bytes = m * 4 * words * 8
-    achieved = alg_bytes / (k1_ms * 1e-3) / 1e9
+    rw = opts.get("resident_words", 0)
     peak, peak_kind = measured_peaks()
-    traffic = profiled_traffic(args.workload, opts["slab_words"] or 16) if world == 1 else None
-    roofline = {"bound": "hbm", "kernel": "stream_kernel", "achieved": achieved, "peak": peak,
-                "peak_source": f"{peak_kind} MEASURED_PEAKS hbm_gbs" if peak_kind == "measured" else "fallback",
-                "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                "achieved_is": "algorithmic bytes (4 row segments per event) / kernel time",
-                "algorithmic_bytes_per_launch": alg_bytes, "kernel_ms": k1_ms}
-    if traffic:  # measured DRAM bytes of the same launch (ncu) over the same time
-        roofline["dram_GBps"] = traffic / (k1_ms * 1e-3) / 1e9
-        roofline["dram_frac"] = roofline["dram_GBps"] / peak
+    if rw:
+        # resident slabs: the rows never leave shared memory; its bytes are the
+        # row loads and stores of every op in every CTA (2 + 2 row words per
+        # op and word), against 128 B per cycle per SM at the sampled clock
+        alg_bytes = stats["ops"] * 4 * words * 8
+        achieved = alg_bytes / (k1_ms * 1e-3) / 1e9
+        sm_mhz = clocks.summary().get("sm_mhz") or 2070.0
+        smem_peak = 128 * 152 * sm_mhz * 1e6 / 1e9
+        roofline = {"bound": "smem", "kernel": "stream_kernel (resident slabs)", "achieved": achieved,
+                    "peak": smem_peak, "peak_source": "derived: 128 B/clock/SM x 152 SMs x median SM clock",
+                    "unit": "GB/s", "frac": achieved / smem_peak, "traffic": None,
+                    "achieved_is": "shared-memory row bytes (2 loads + 2 stores of a row word per op and "
+                                   "column word) / kernel time; the per-level latency, not bandwidth, bounds it",
+                    "algorithmic_bytes_per_launch": alg_bytes, "kernel_ms": k1_ms}
+    else:
+        alg_bytes = m * 4 * words * 8
+        achieved = alg_bytes / (k1_ms * 1e-3) / 1e9
+        traffic = profiled_traffic(args.workload, opts["slab_words"] or 16) if world == 1 else None
+        roofline = {"bound": "hbm", "kernel": "stream_kernel", "achieved": achieved, "peak": peak,
+                    "peak_source": f"{peak_kind} MEASURED_PEAKS hbm_gbs" if peak_kind == "measured" else "fallback",
+                    "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                    "achieved_is": "algorithmic bytes (4 row segments per event) / kernel time",
+                    "algorithmic_bytes_per_launch": alg_bytes, "kernel_ms": k1_ms}
+        if traffic:  # measured DRAM bytes of the same launch (ncu) over the same time
+            roofline["dram_GBps"] = traffic / (k1_ms * 1e-3) / 1e9
+            roofline["dram_frac"] = roofline["dram_GBps"] / peak
 
     result = {"metric": METRIC, "value": value, "unit": "bit-updates/s", "n_gpus": world, "steps": args.steps,
               "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "strong",
@@ -1172,9 +1195,11 @@ def main():
                          "parallelism": f"source columns split over {world} GPUs, sizes all-gathered"
                                         if world > 1 else "single GPU",
                          "l2": "inputs larger than L2 (S %.2f GB, events %.0f MB)" % (n * W * 8 / 1e9, m * 16 / 1e6),
-                         "window_events": opts["window_events"] or 640, "slab_words": opts["slab_words"] or 16,
-                         "smem_rows": opts["smem_rows"] or "default",
-                         "ctas": -(-tn.tn_row_words(ncols) // (opts["slab_words"] or 16)),
+                         "window_events": opts["window_events"] or 640,
+                         "slab_words": None if rw else (opts["slab_words"] or 16),
+                         "smem_rows": None if rw else (opts["smem_rows"] or "default"),
+                         "resident_words": rw or None,
+                         "ctas": -(-words // rw) if rw else -(-tn.tn_row_words(ncols) // (opts["slab_words"] or 16)),
                          "autotuned": tuned is not None,
                          "levels": stats["levels"], "ops": stats["ops"], "windows": stats["windows"],
                          "global_memory_windows": stats["windows"] - stats["local_windows"]},
