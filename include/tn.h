@@ -227,9 +227,10 @@ typedef struct tn_plan_options {
 
 /* Largest node count n whose rows fit the resident-slab form at
  * `resident_words` (1 or 2) 64-bit words per row, with no saved rows (a
- * plan whose tie groups need saved rows needs room for them too); 0 for an
- * unsupported width.  Host-only, no device call besides the first query of the
- * current device's shared-memory limit. */
+ * plan whose tie groups need saved rows needs room for them too): 24,928 and
+ * 12,464 on a GB300.  0 for an unsupported width, or when the current device
+ * cannot be queried.  No device work: the first call per device queries its
+ * shared-memory limit. */
 uint32_t tn_resident_max_rows(uint32_t resident_words);
 
 typedef struct tn_plan_stats {
