@@ -472,7 +472,10 @@ typedef struct tn_server tn_server;
 typedef struct tn_server_options {
     uint64_t memory_budget; /* device bytes for resident jobs (0 = 60 % of free memory) */
     uint32_t max_active;    /* jobs resident at once (0 = 16) */
-    uint32_t window_events; /* plan options of every batch (0 = defaults) */
+    uint32_t window_events; /* plan options of every batch (0 = windows of 576 events and a
+                               144 KB row buffer, which leave room on each SM for the
+                               scheduling CTAs of other jobs' batches beside a running
+                               update CTA; else this window and the default buffer) */
     uint32_t slab_words;    /* 0 = per job: the widest even slab (at most 16 words)
                                that still gives the job 16 CTAs, at least 2 words */
     uint32_t workers;       /* host worker threads (0 = 16): admission, copies in,

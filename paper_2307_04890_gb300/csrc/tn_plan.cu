@@ -1025,7 +1025,9 @@ static tn_status plan_create_impl(const uint32_t *u, const uint32_t *v, const in
     TN_STEP(alloc_async(&base, 3ull * a.nw, st));
     TN_STEP(alloc_async(&d_tot, 1, st));
     tn_internal_count_launches(1);
-    window_scan_kernel<<<1, 1024, 0, st>>>(a.wcount, a.nw, base, d_tot);
+    // 256 threads: the single scan CTA then fits an SM beside a running streaming
+    // CTA (registers), instead of waiting for a free SM
+    window_scan_kernel<<<1, 256, 0, st>>>(a.wcount, a.nw, base, d_tot);
     TN_STEP(cudaGetLastError());
     TN_STEP(cudaMemcpyAsync(&host_tot, d_tot, sizeof(Totals), cudaMemcpyDeviceToHost, st));
     TN_STEP(tn_internal_stream_wait(st));

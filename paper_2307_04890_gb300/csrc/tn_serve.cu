@@ -125,6 +125,9 @@ namespace {
 // Slab width of a job when the server options leave it open: a small matrix
 // still gets at least 16 CTAs (every CTA streams all of the job's events, so
 // narrower slabs shorten the job), large ones keep 16-word slabs.
+constexpr uint32_t kServeWindow = 576;
+constexpr uint32_t kServeRowBytes = 144 * 1024;
+
 uint32_t serve_slab_words(uint32_t n)
 {
     const uint64_t ld = tn_row_words(n);
@@ -231,6 +234,15 @@ tn_status start_job(tn_server *s, ServeJob *j)
     memset(&opt, 0, sizeof(opt));
     opt.window_events = s->opt.window_events;
     opt.slab_words = s->opt.slab_words ? s->opt.slab_words : serve_slab_words(j->n);
+    if (!opt.window_events) {
+        // Room on every SM for the scheduler's CTAs beside a running update
+        // CTA, so that a batch's schedule does not wait for an SM to free up:
+        // windows of kServeWindow events (a 36 KB scheduling arena) and a row
+        // buffer of kServeRowBytes (the 2 x kServeWindow rows such a window can
+        // touch, at 16-word slabs)
+        opt.window_events = kServeWindow;
+        opt.smem_rows = kServeRowBytes / (8u * opt.slab_words);
+    }
     rc = tn_online_create(j->n, &opt, sl->ast, &j->on);
     if (rc != TN_OK) return rc;
     rc = tn::online_use_apply_stream(j->on, sl->ast);
