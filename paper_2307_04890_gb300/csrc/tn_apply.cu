@@ -627,6 +627,10 @@ __device__ void resident_slab(const Job &J, uint32_t smem_bytes, uint8_t *smem, 
     while (nst > fit) nst >>= 1;
     const uint32_t smask = nst - 1, sshift = __ffs(nst) - 1;
     const uint64_t w0 = J.w_begin + (uint64_t)cta * RW;
+    // Every chunk of the blob holds part of some item: windows' regions and
+    // records are whole 16-byte units, so a window's padding unit (after an odd
+    // number of ops) sits at an odd offset and never begins a chunk.  Every
+    // chunk the producer copies is therefore waited for and released.
     const uint32_t nchunks = (uint32_t)((blob8 + kChunk8 - 1) / kChunk8);
     const uint32_t C = consumers() < kResidentConsumers ? consumers() : kResidentConsumers;
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
