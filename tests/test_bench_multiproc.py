@@ -155,3 +155,16 @@ def test_reference_arm_of_the_online_workload():
     assert rec["impl"] == "reference" and rec["unit"] == "events/s" and rec["value"] > 0
     assert rec["metric"].startswith("events/s through the online state")
     assert rec["cpu_baseline"]["kind"] == "oracle" and rec["e2e"]["unit"] == "events/s"
+
+
+def test_reference_arm_of_the_er_small_workload():
+    """The ER n = 10^4 workload (the resident-slab form's bench line) has a
+    reference arm: the oracle over seeded column blocks of the same events."""
+    cmd = [sys.executable, "bench.py", "--impl", "reference", "--workload", "er-small", "--steps", "1",
+           "--warmup", "0", "--cpu-seconds", "0.5"]
+    res = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert res.returncode == 0, res.stderr[-2000:]
+    rec = json.loads([ln for ln in res.stdout.splitlines() if ln.startswith("{")][-1])
+    assert rec["impl"] == "reference" and rec["unit"] == "bit-updates/s" and rec["value"] > 0
+    assert rec["config"]["n"] == 10_000 and rec["config"]["m"] == 10_000_000
+    assert rec["cpu_baseline"]["kind"] == "oracle"
