@@ -140,6 +140,36 @@ def gather_sizes(local, local_argmax, n, rank, world, dist):
     return full, -neg_id
 
 
+def gather_blocks(local, total, rank, world, dist):
+    """All-gather of contiguous per-rank blocks (rank r holds entries
+    column_range(total, r, world)) into the whole array, in rank order."""
+    import torch
+    if world == 1 or dist is None:
+        return local
+    counts = [column_range(total, r, world)[1] - column_range(total, r, world)[0] for r in range(world)]
+    buf = torch.zeros(max(counts), dtype=local.dtype, device=local.device)
+    buf[: local.numel()] = local
+    parts = [torch.empty_like(buf) for _ in range(world)]
+    dist.all_gather(parts, buf)
+    return torch.cat([parts[r][: counts[r]] for r in range(world)])
+
+
+def replica_owner(j, world):
+    """Rank that builds hash replica j when the hashed workload is split over
+    ranks: the R proxy networks are independent (Section 4.2), dealt round-robin."""
+    return j % world
+
+
+def share_proxies(P, R, world, dist):
+    """Every rank receives every proxy matrix from the rank that built it (one
+    broadcast per replica): the fusion of Section 4.2 intersects all R replicas
+    for every source, so this is the split's one exchange step."""
+    if world == 1 or dist is None:
+        return
+    for j in range(R):
+        dist.broadcast(P[j], src=replica_owner(j, world))
+
+
 def replica_seed(w, rank):
     """Rank r runs an independent replica of the workload (weak scaling), seeded apart."""
     return w["seed"] + 1000 * rank
@@ -647,15 +677,22 @@ def run_hashed(args, w, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     n, m, k, R, nsrc = w["n"], w["m"], w["k"], w["R"], w["nsrc"]
-    u, v, t = make_events(w, rank)
-    rng = np.random.default_rng(w["seed"] + 1000 * rank)
+    # one job over all ranks: the same events and sampled sources everywhere;
+    # rank r builds the replicas it owns and the exact columns of its share of
+    # the sources, receives the other replicas' matrices, and fuses its share
+    u, v, t = make_events(w)
+    rng = np.random.default_rng(w["seed"])
     src_np = np.sort(rng.choice(n, nsrc, replace=False)).astype(np.uint32)
+    mine = [j for j in range(R) if replica_owner(j, world) == rank]
+    s0, s1 = column_range(nsrc, rank, world)
+    ns = s1 - s0
     du = torch.from_numpy(u.view(np.int32)).to(dev)
     dv = torch.from_numpy(v.view(np.int32)).to(dev)
     dt = torch.from_numpy(t).to(dev)
-    src = torch.from_numpy(src_np.view(np.int32)).to(dev)
+    src_all = torch.from_numpy(src_np.view(np.int32)).to(dev)
+    src = src_all[s0:s1]
     P = torch.empty((R, k, tn.tn_row_words(k)), dtype=torch.int64, device=dev)
-    Sx = torch.empty((n, tn.tn_row_words(nsrc)), dtype=torch.int64, device=dev)
+    Sx = torch.empty((n, tn.tn_row_words(ns)), dtype=torch.int64, device=dev)
     stream = torch.cuda.current_stream(dev)
     seed = 0  # replica j hashes with splitmix64(seed ^ j): seeds 0..R-1
     ev = lambda: torch.cuda.Event(enable_timing=True)
@@ -666,16 +703,20 @@ def run_hashed(args, w, rank, world, local_rank):
 
     def step(record):
         H, pu, pv = tn.tn_hash_proxy(du, dv, n, k, R, seed)                              # a5
-        plans = [tn.Plan(pu[j].contiguous(), pv[j].contiguous(), dt, k, **popts) for j in range(R)]  # a1 (proxies)
+        plans = [tn.Plan(pu[j].contiguous(), pv[j].contiguous(), dt, k, **popts) for j in mine]  # a1 (proxies)
         plan_x = tn.Plan(du, dv, dt, n, **xopts)                                          # a1 (exact sample)
         e = [ev() for _ in range(3)]
         e[0].record(stream)
-        tn.tn_plan_apply_batch(plans + [plan_x], [P[j] for j in range(R)] + [Sx],         # a2 + a3 + a6, and
-                               ncols=[k] * R + [nsrc], init=True, srcs=[None] * R + [src])  # a8's exact columns
+        tn.tn_plan_apply_batch(plans + [plan_x], [P[j] for j in mine] + [Sx],             # a2 + a3 + a6, and
+                               ncols=[k] * len(mine) + [ns], init=True,                   # a8's exact columns
+                               srcs=[None] * len(mine) + [src])
         e[1].record(stream)
+        share_proxies(P, R, world, dist)                                                  # (N > 1)
         est = tn.tn_hash_estimate(P, R, k, H, n, src=src)                                 # a7
         e[2].record(stream)
-        exact, _, _ = tn.tn_out_sizes(Sx, n, nsrc)
+        exact, _, _ = tn.tn_out_sizes(Sx, n, ns)
+        est = gather_blocks(est, nsrc, rank, world, dist)                                 # (N > 1)
+        exact = gather_blocks(exact, nsrc, rank, world, dist)
         err = tn.tn_error_stats(est, exact, n)                                            # a8 (synchronises)
         if record:
             timing["combined_ms"].append(e[0].elapsed_time(e[1]))
@@ -703,82 +744,91 @@ def run_hashed(args, w, rank, world, local_rank):
     ms_total = job_max_ms(start.elapsed_time(end), dist, dev)
     ms_step = ms_total / args.steps
 
-    # the same work in separate launches, each at its own best shape (the proxies alone:
-    # 8-word slabs in 80 KB row buffers, two 4-warp CTAs per SM; the exact columns:
-    # the defaults), and the proxies as a graph vs one launch each
-    P_ref, Sx_ref = P.clone(), Sx.clone()
+    # beside the step, on one GPU: the same work in separate launches, the graph
+    # replay against single launches, and the error on unsaturated prefixes
+    proxies_alone_ms = exact_alone_ms = graph_ms = single_ms = None
+    separate_identical = identical = None
     sopts = dict(slab_words=8, window_events=640, smem_rows=80 * 1024 // (8 * 8))
-    plans = [tn.Plan(pu[j].contiguous(), pv[j].contiguous(), dt, k, **sopts) for j in range(R)]
-    plan_x = tn.Plan(du, dv, dt, n, **xopts)
-    e0, e1, e2 = ev(), ev(), ev()
-    e0.record(stream)
-    tn.tn_plan_apply_batch(plans, [P[j] for j in range(R)], init=True)
-    e1.record(stream)
-    plan_x.apply(Sx, ncols=nsrc, src=src, init=True)
-    e2.record(stream)
-    torch.cuda.synchronize()
-    proxies_alone_ms, exact_alone_ms = e0.elapsed_time(e1), e1.elapsed_time(e2)
-    separate_identical = bool(torch.equal(P, P_ref) and torch.equal(Sx, Sx_ref))
-    g = tn.BatchGraph(plans, [P[j] for j in range(R)])
-    g.launch()
-    torch.cuda.synchronize()
-    e0.record(stream)
-    g.launch()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    graph_ms = e0.elapsed_time(e1)
-    P2 = torch.empty_like(P)
-    e0.record(stream)
-    for j in range(R):
-        plans[j].apply(P2[j], init=True)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    single_ms = e0.elapsed_time(e1)
-    identical = bool(torch.equal(P, P_ref) and torch.equal(P2, P_ref))
-    g.destroy()
-    for p in plans:
-        p.destroy()
-    plan_x.destroy()
-    del P2, P_ref, Sx_ref
-
-    # error on unsaturated prefixes of the stream (to a group boundary)
     keys = ("mean_abs", "max_abs", "mean_rel", "max_rel", "w1")
     prefixes = []
-    for want in (10_000, 100_000, 1_000_000):
-        mp = group_prefix(t, want)
-        Hp, pup, pvp = tn.tn_hash_proxy(du[:mp], dv[:mp], n, k, R, seed)
-        plans_p = [tn.Plan(pup[j].contiguous(), pvp[j].contiguous(), dt[:mp], k, **popts) for j in range(R)]
-        plan_xp = tn.Plan(du[:mp], dv[:mp], dt[:mp], n, **xopts)
-        tn.tn_plan_apply_batch(plans_p + [plan_xp], [P[j] for j in range(R)] + [Sx], ncols=[k] * R + [nsrc],
-                               init=True, srcs=[None] * R + [src])
-        est_p = tn.tn_hash_estimate(P, R, k, Hp, n, src=src)
-        exact_p, _, _ = tn.tn_out_sizes(Sx, n, nsrc)
-        err_p = tn.tn_error_stats(est_p, exact_p, n)
-        prefixes.append(dict({key: err_p[key] for key in keys}, events=mp,
-                             mean_exact=float(exact_p.float().mean().item()),
-                             mean_estimate=float(est_p.float().mean().item())))
-        for p in plans_p + [plan_xp]:
+    if world == 1:
+        # the same work in separate launches, each at its own best shape (the proxies alone:
+        # 8-word slabs in 80 KB row buffers, two 4-warp CTAs per SM; the exact columns:
+        # the defaults), and the proxies as a graph vs one launch each
+        P_ref, Sx_ref = P.clone(), Sx.clone()
+        plans = [tn.Plan(pu[j].contiguous(), pv[j].contiguous(), dt, k, **sopts) for j in range(R)]
+        plan_x = tn.Plan(du, dv, dt, n, **xopts)
+        e0, e1, e2 = ev(), ev(), ev()
+        e0.record(stream)
+        tn.tn_plan_apply_batch(plans, [P[j] for j in range(R)], init=True)
+        e1.record(stream)
+        plan_x.apply(Sx, ncols=nsrc, src=src, init=True)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        proxies_alone_ms, exact_alone_ms = e0.elapsed_time(e1), e1.elapsed_time(e2)
+        separate_identical = bool(torch.equal(P, P_ref) and torch.equal(Sx, Sx_ref))
+        g = tn.BatchGraph(plans, [P[j] for j in range(R)])
+        g.launch()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        g.launch()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        graph_ms = e0.elapsed_time(e1)
+        P2 = torch.empty_like(P)
+        e0.record(stream)
+        for j in range(R):
+            plans[j].apply(P2[j], init=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        single_ms = e0.elapsed_time(e1)
+        identical = bool(torch.equal(P, P_ref) and torch.equal(P2, P_ref))
+        g.destroy()
+        for p in plans:
             p.destroy()
+        plan_x.destroy()
+        del P2, P_ref, Sx_ref
+
+        # error on unsaturated prefixes of the stream (to a group boundary)
+        for want in (10_000, 100_000, 1_000_000):
+            mp = group_prefix(t, want)
+            Hp, pup, pvp = tn.tn_hash_proxy(du[:mp], dv[:mp], n, k, R, seed)
+            plans_p = [tn.Plan(pup[j].contiguous(), pvp[j].contiguous(), dt[:mp], k, **popts) for j in range(R)]
+            plan_xp = tn.Plan(du[:mp], dv[:mp], dt[:mp], n, **xopts)
+            tn.tn_plan_apply_batch(plans_p + [plan_xp], [P[j] for j in range(R)] + [Sx], ncols=[k] * R + [nsrc],
+                                   init=True, srcs=[None] * R + [src])
+            est_p = tn.tn_hash_estimate(P, R, k, Hp, n, src=src)
+            exact_p, _, _ = tn.tn_out_sizes(Sx, n, nsrc)
+            err_p = tn.tn_error_stats(est_p, exact_p, n)
+            prefixes.append(dict({key: err_p[key] for key in keys}, events=mp,
+                                 mean_exact=float(exact_p.float().mean().item()),
+                                 mean_estimate=float(est_p.float().mean().item())))
+            for p in plans_p + [plan_xp]:
+                p.destroy()
 
     combined_ms = statistics.mean(timing["combined_ms"])
     wx = tn.tn_row_words(nsrc)
-    alg_exact = m * 4 * ((nsrc + 63) // 64) * 8
-    alg_proxy = R * m * 4 * ((k + 63) // 64) * 8
+    # this rank's launch: its replicas and its share of the sampled columns
+    alg_exact = m * 4 * ((ns + 63) // 64) * 8
+    alg_proxy = len(mine) * m * 4 * ((k + 63) // 64) * 8
     peak, peak_kind = measured_peaks()
-    bit_updates = (R * k + nsrc) * m
-    result = {"metric": METRIC + " (hashed estimate)", "value": world * m / (ms_step * 1e-3), "unit": "events/s",
+    bit_updates = (R * k + nsrc) * m  # the whole job
+    result = {"metric": METRIC + " (hashed estimate)", "value": m / (ms_step * 1e-3), "unit": "events/s",
               "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
-              "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+              "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "u64",
               "data": "synthetic",
               "config": {"workload": w["desc"], "n": n, "m": m, "k": k, "R": R, "sampled_sources": nsrc,
                          "plan_options": {"proxies": popts, "exact_sampled": xopts},
-                         "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                         "parallelism": (f"{world} GPUs: replicas dealt round-robin and broadcast to every rank, "
+                                         "sampled sources split, estimates and sizes all-gathered")
+                                        if world > 1 else "single GPU",
                          "l2": "inputs larger than L2 (events 1.6 GB, sampled matrix %.1f GB)" % (n * wx * 8 / 1e9)},
-              "bit_updates_per_s": world * bit_updates / (ms_step * 1e-3),
+              "bit_updates_per_s": bit_updates / (ms_step * 1e-3),
               "kernels_ms": {"proxies_and_exact_columns_one_launch": combined_ms,
                              "estimate": statistics.mean(timing["estimate_ms"]),
                              "proxies_alone": proxies_alone_ms, "exact_columns_alone": exact_alone_ms},
-              "roofline": {"bound": "hbm", "kernel": "stream_kernel (8 proxies + 65,536 exact columns, one launch)",
+              "roofline": {"bound": "hbm", "kernel": "stream_kernel (%d proxies + %d exact columns, one launch)"
+                                                     % (len(mine), ns),
                            "achieved": (alg_exact + alg_proxy) / (combined_ms * 1e-3) / 1e9, "peak": peak,
                            "peak_source": f"{peak_kind} MEASURED_PEAKS hbm_gbs", "unit": "GB/s",
                            "frac": (alg_exact + alg_proxy) / (combined_ms * 1e-3) / 1e9 / peak, "traffic": None,

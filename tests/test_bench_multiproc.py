@@ -3,11 +3,13 @@
 The exact workloads split the source columns over the ranks (columns never
 interact, Section 3.1): every rank streams all events over its own block of
 columns and the out-sizes are all-gathered, with the largest out-component
-taken over the gathered sizes.  Here each rank computes its block with the
-oracle and runs bench.py's gather.  The hashed and online workloads run
-independent replicas (different seeds); the job's time is the slowest rank's
-(all-reduce MAX); under torchrun only rank 0 of the reference arm prints its
-line.
+taken over the gathered sizes.  The hashed workload deals its R replicas over
+the ranks, broadcasts every proxy matrix to every rank (the fusion intersects
+all replicas, Section 4.2) and splits the sampled sources; estimates and exact
+sizes are all-gathered.  Here each rank computes its share with the oracle and
+runs bench.py's exchange steps.  The online workload runs independent
+replicas (different seeds); the job's time is the slowest rank's (all-reduce
+MAX); under torchrun only rank 0 of the reference arm prints its line.
 """
 import json
 import os
@@ -168,3 +170,62 @@ def test_reference_arm_of_the_er_small_workload():
     assert rec["impl"] == "reference" and rec["unit"] == "bit-updates/s" and rec["value"] > 0
     assert rec["config"]["n"] == 10_000 and rec["config"]["m"] == 10_000_000
     assert rec["cpu_baseline"]["kind"] == "oracle"
+
+
+def _hashed_rank_main(rank, world, port, out_dir):
+    import torch
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle
+    from paper_2307_04890_gb300 import synth
+
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    n, m, k, R, seed, nsrc = 2000, 20_000, 97, 5, 3, 301
+    u, v, t = synth.uniform_events(n, m, t_range=8000, seed=21)  # the same events on every rank
+    src = np.sort(np.random.default_rng(4).choice(n, nsrc, replace=False)).astype(np.uint32)
+    H = oracle.hash_nodes(seed, R, k, n)  # every rank hashes with all R replicas
+    W = (k + 63) // 64
+    P = torch.zeros((R, k, W), dtype=torch.int64)
+    for j in range(R):  # this rank builds the replicas it owns
+        if bench.replica_owner(j, world) == rank:
+            P[j] = torch.from_numpy(oracle.proxy_matrices(u, v, t, H[j:j + 1], k)[0].view(np.int64))
+    bench.share_proxies(P, R, world, dist)
+    s0, s1 = bench.column_range(nsrc, rank, world)
+    Pn = P.numpy().view(np.uint64)
+    est = torch.from_numpy(oracle.hash_estimate(Pn, H, n, src[s0:s1]).view(np.int32))
+    exact = torch.from_numpy(oracle.column_counts(oracle.component_matrix(u, v, t, n, src[s0:s1]),
+                                                  s1 - s0).view(np.int32))
+    est = bench.gather_blocks(est, nsrc, rank, world, dist)
+    exact = bench.gather_blocks(exact, nsrc, rank, world, dist)
+    np.save(os.path.join(out_dir, f"P{rank}.npy"), Pn)
+    np.save(os.path.join(out_dir, f"est{rank}.npy"), est.numpy().view(np.uint32))
+    np.save(os.path.join(out_dir, f"exact{rank}.npy"), exact.numpy().view(np.uint32))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_hashed_split_equals_the_whole_job(tmp_path, world):
+    """R = 5 replicas dealt over 2 or 3 ranks (uneven), 301 sampled sources
+    split: after the broadcasts every rank holds all R proxy matrices, and the
+    gathered estimates and exact sizes equal the single-process oracle's."""
+    import torch.multiprocessing as mp
+    import oracle
+    from paper_2307_04890_gb300 import synth
+
+    port = free_port()
+    mp.start_processes(_hashed_rank_main, args=(world, port, str(tmp_path)), nprocs=world, join=True,
+                       start_method="spawn")
+    n, m, k, R, seed, nsrc = 2000, 20_000, 97, 5, 3, 301
+    u, v, t = synth.uniform_events(n, m, t_range=8000, seed=21)
+    src = np.sort(np.random.default_rng(4).choice(n, nsrc, replace=False)).astype(np.uint32)
+    H = oracle.hash_nodes(seed, R, k, n)
+    Pref = oracle.proxy_matrices(u, v, t, H, k)
+    want_est = oracle.hash_estimate(Pref, H, n, src)
+    want_exact = oracle.column_counts(oracle.component_matrix(u, v, t, n, src), nsrc)
+    assert (want_est >= want_exact).all() and (want_est > want_exact).any()  # a non-trivial estimate
+    for r in range(world):
+        assert np.array_equal(np.load(tmp_path / f"P{r}.npy"), Pref)
+        assert np.array_equal(np.load(tmp_path / f"est{r}.npy"), want_est)
+        assert np.array_equal(np.load(tmp_path / f"exact{r}.npy"), want_exact)
