@@ -434,7 +434,7 @@ def run_reference_hashed(args, w, world):
               f"{threads} threads (one proxy network each)")
     line = {"impl": "reference", "metric": METRIC + " (hashed estimate)", "value": value, "unit": "events/s",
             "n_gpus": world, "steps": 1, "warmup": 0, "ms_per_step": spent * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "scaling": "strong", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": w["desc"], "n": n, "m": w["m"], "k": k, "R": R},
             "cpu_baseline": {"value": value, "unit": "events/s", "cores": threads, "kind": "oracle", "sample": sample,
                              "nproc": os.cpu_count(), "cpu_model": cpu_model()},
