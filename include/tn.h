@@ -209,7 +209,9 @@ typedef struct tn_plan_options {
                                below ceil(row words / slab_words) is raised to it */
     uint32_t resident_words;/* 0: the column-slab form above (rows move between HBM and
                                shared memory).  1 or 2: the resident-slab form for
-                               small networks: each CTA keeps resident_words 64-bit
+                               small networks, the same update of Algorithm 1
+                               (Section 3.1) in another launch shape: each CTA keeps
+                               resident_words 64-bit
                                words of EVERY row (and of the tie groups' saved rows)
                                in shared memory for the whole batch and reads only the
                                schedule, so the matrix is read and written once per
@@ -225,7 +227,8 @@ typedef struct tn_plan_options {
     uint32_t reserved[2];   /* must be zero */
 } tn_plan_options;
 
-/* Largest node count n whose rows fit the resident-slab form at
+/* A launch-shape helper with no counterpart in the paper: the largest node
+ * count n whose rows fit the resident-slab form at
  * `resident_words` (1 or 2) 64-bit words per row, with no saved rows (a
  * plan whose tie groups need saved rows needs room for them too): 24,928 and
  * 12,464 on a GB300.  0 for an unsupported width, or when the current device
